@@ -1,0 +1,182 @@
+"""Finite-difference diffusion matrices, box partitions and seeded vectors.
+
+Conventions (one reading of Section 6, where the paper uses finite elements):
+  * Dirichlet boundary nodes are eliminated; only interior nodes are unknowns.
+  * Lexicographic numbering idx = i + nx*(j + ny*k).
+  * Stencils are unscaled by h^2: 5-point [4; -1 x 4], 7-point [6; -1 x 6].
+  * Variable coefficient: node-wise kappa, face coefficient is the harmonic
+    mean 2 k_i k_j / (k_i + k_j), a face to the boundary uses k_i, and the
+    diagonal is the sum of the face coefficients of the node.
+  * CSR arrays: rowptr int32 (n+1), col int32 (nnz, ascending within a row),
+    val float64 (nnz).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _stencil_csr(shape, face_coef):
+    """Assemble the CSR matrix of a nearest-neighbour stencil on a box grid.
+
+    shape     -- (nx,) (nx, ny) or (nx, ny, nz) interior grid
+    face_coef -- callable(axis, lo_mask_index_arrays) -> see below; here a list
+                 per axis of arrays c_minus, c_plus of shape `shape` giving the
+                 coefficient of the face towards -axis / +axis of each node
+                 (the boundary faces included: they add to the diagonal only).
+    """
+    dims = len(shape)
+    n = int(np.prod(shape))
+    # lexicographic: first axis fastest
+    strides = [1]
+    for d in range(1, dims):
+        strides.append(strides[-1] * shape[d - 1])
+    idx = np.arange(n, dtype=np.int64).reshape(shape[::-1])  # (nz, ny, nx)
+    coords = np.unravel_index(np.arange(n), shape[::-1])      # arrays k, j, i
+    coords = coords[::-1]                                       # i, j, k order
+    c_minus, c_plus = face_coef
+    diag = np.zeros(n)
+    for d in range(dims):
+        diag += c_minus[d].reshape(-1) + c_plus[d].reshape(-1)
+    # neighbour slots in ascending column order:
+    # -z, -y, -x, self, +x, +y, +z  (for lexicographic numbering)
+    cols = []
+    vals = []
+    valid = []
+    for d in reversed(range(dims)):
+        ok = coords[d] > 0
+        cols.append(np.arange(n, dtype=np.int64) - strides[d])
+        vals.append(-c_minus[d].reshape(-1))
+        valid.append(ok)
+    cols.append(np.arange(n, dtype=np.int64))
+    vals.append(diag)
+    valid.append(np.ones(n, dtype=bool))
+    for d in range(dims):
+        ok = coords[d] < shape[d] - 1
+        cols.append(np.arange(n, dtype=np.int64) + strides[d])
+        vals.append(-c_plus[d].reshape(-1))
+        valid.append(ok)
+    cols = np.stack(cols, axis=1)
+    vals = np.stack(vals, axis=1)
+    valid = np.stack(valid, axis=1)
+    counts = valid.sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    if rowptr[-1] >= 2**31:
+        raise ValueError("matrix too large for int32 row pointers")
+    col = cols[valid].astype(np.int32)
+    val = vals[valid].astype(np.float64)
+    del idx
+    return rowptr.astype(np.int32), col, val
+
+
+def poisson2d(nx: int, ny: int):
+    """5-point Dirichlet Laplacian on an nx x ny interior grid (unscaled)."""
+    shape = (nx, ny)
+    ones = np.ones(shape[::-1])
+    c = [ones, ones]
+    return _stencil_csr(shape, (c, c))
+
+
+def poisson3d(nx: int, ny: int, nz: int):
+    """7-point Dirichlet Laplacian on an nx x ny x nz interior grid (unscaled)."""
+    shape = (nx, ny, nz)
+    ones = np.ones(shape[::-1])
+    c = [ones, ones, ones]
+    return _stencil_csr(shape, (c, c))
+
+
+def diffusion3d(kappa: np.ndarray):
+    """7-point -div(kappa grad u) with node-wise kappa of shape (nz, ny, nx).
+
+    Face coefficient between nodes i and j: 2 k_i k_j / (k_i + k_j); a face
+    to the Dirichlet boundary uses k_i.
+    """
+    k = np.asarray(kappa, dtype=np.float64)
+    nz, ny, nx = k.shape
+    shape = (nx, ny, nz)
+    c_minus = []
+    c_plus = []
+    for d, ax in zip(range(3), (2, 1, 0)):  # d: x,y,z  -> array axis
+        km = k.copy()
+        kp = k.copy()
+        sl_lo = [slice(None)] * 3
+        sl_hi = [slice(None)] * 3
+        sl_lo[ax] = slice(0, -1)
+        sl_hi[ax] = slice(1, None)
+        a = k[tuple(sl_lo)]
+        b = k[tuple(sl_hi)]
+        h = 2.0 * a * b / (a + b)
+        kp[tuple(sl_lo)] = h
+        km[tuple(sl_hi)] = h
+        c_minus.append(km)
+        c_plus.append(kp)
+    return _stencil_csr(shape, (c_minus, c_plus))
+
+
+def checkerboard_kappa(n: int, blocks: int, seed: int, values=(1.0, 1e3)):
+    """Piecewise-constant kappa on an n^3 grid: blocks^3 cubes, i.i.d. values."""
+    rng = np.random.default_rng(seed)
+    pick = rng.integers(0, 2, size=(blocks, blocks, blocks))
+    table = np.asarray(values, dtype=np.float64)[pick]
+    edge = -(-n // blocks)
+    k = np.repeat(np.repeat(np.repeat(table, edge, 0), edge, 1), edge, 2)
+    return np.ascontiguousarray(k[:n, :n, :n])
+
+
+def box_partition(shape, box):
+    """Subdomain id of every unknown for a partition into boxes.
+
+    shape -- interior grid (nx, ny[, nz]); box -- box edge lengths.
+    Boxes are numbered lexicographically (first axis fastest), like unknowns.
+    Returns (part int32[n], nsub).
+    """
+    shape = tuple(int(s) for s in shape)
+    box = tuple(int(b) for b in box)
+    nb = [-(-s // b) for s, b in zip(shape, box)]
+    grids = np.meshgrid(*[np.arange(s) // b for s, b in zip(shape, box)],
+                        indexing="ij")  # each of shape `shape`
+    pid = np.zeros(shape, dtype=np.int64)
+    mult = 1
+    for d in range(len(shape)):
+        pid += grids[d] * mult
+        mult *= nb[d]
+    # flatten in lexicographic order (first axis fastest)
+    part = pid.transpose(tuple(reversed(range(len(shape))))).reshape(-1)
+    return part.astype(np.int32), int(mult)
+
+
+def uniform_rhs(n: int, seed: int):
+    """b ~ U[-1, 1] from numpy.random.default_rng(seed)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
+
+
+def grid_shape_of(name: str):
+    return WORKLOADS[name]["shape"]
+
+
+WORKLOADS = {
+    # 2D 5-point Poisson 64x64, 4x4 boxes of 16x16, padding 1 on every level
+    "poisson2d_64": dict(shape=(64, 64), box=(16, 16), padding=1, n_fac=2),
+    # 3D 7-point Poisson 128^3, 8x8x8 boxes of 16^3, padding 2 on every level
+    "poisson3d_128": dict(shape=(128, 128, 128), box=(16, 16, 16), padding=2,
+                          n_fac=2),
+}
+
+
+def workload(name: str, seed: int = 0, shape=None, box=None):
+    """Matrix, partition and right-hand side of a named synthetic workload."""
+    w = dict(WORKLOADS[name])
+    if shape is not None:
+        w["shape"] = tuple(shape)
+    if box is not None:
+        w["box"] = tuple(box)
+    shape = w["shape"]
+    if len(shape) == 2:
+        rp, ci, v = poisson2d(*shape)
+    else:
+        rp, ci, v = poisson3d(*shape)
+    part, nsub = box_partition(shape, w["box"])
+    b = uniform_rhs(int(np.prod(shape)), seed)
+    return dict(rowptr=rp, col=ci, val=v, part=part, nsub=nsub, b=b,
+                padding=w["padding"], n_fac=w["n_fac"], shape=shape,
+                box=w["box"], name=name, seed=seed)

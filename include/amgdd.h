@@ -1,0 +1,205 @@
+/*
+ * amgdd.h - C ABI of the GB300 AMG-DD solve-phase library.
+ *
+ * Method: algebraic multigrid domain decomposition (AMG-DD) of Mitchell,
+ * Strzodka and Falgout, "Parallel Performance of Algebraic Multigrid Domain
+ * Decomposition" (arXiv 1906.10575). On one GPU the paper's processors become
+ * virtual subdomains: every composite grid is solved by the same kernel launch.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an amgdd_status and never aborts, traps or exits.
+ *     On failure amgdd_last_error(h) describes the cause (thread-local text
+ *     when no handle exists yet).
+ *   - Host pointers are caller-owned and only read during the call, unless
+ *     stated otherwise. Device pointers are caller-owned CUDA global-memory
+ *     buffers (for example torch tensor storage) on the current device.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream. Device work is ordered on that stream; calls that
+ *     return host data synchronise it.
+ *   - Values are IEEE FP64, indices int32. Matrices are CSR with ascending,
+ *     unique column indices in each row.
+ *   - Every row product in the solve phase is computed as the chain
+ *     s = 0; s = fma(a_ik, x_k, s) over ascending column index k, so results
+ *     do not depend on the kernel's launch shape.
+ *   - One handle may be used by one host thread / stream at a time.
+ */
+#ifndef AMGDD_H
+#define AMGDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amgdd_handle_s *amgdd_handle;
+
+typedef enum {
+    AMGDD_OK = 0,
+    AMGDD_ERR_INVALID_ARG = 1,         /* bad size, pointer, range or CSR structure */
+    AMGDD_ERR_NOT_SYMMETRIC = 2,       /* A is not structurally/numerically symmetric */
+    AMGDD_ERR_HIERARCHY_ASSUMPTION = 3,/* connectivity assumption of Sections 4.2/4.5 fails */
+    AMGDD_ERR_OOM = 4,                 /* host or device allocation failed */
+    AMGDD_ERR_CUDA = 5,                /* a CUDA runtime call failed */
+    AMGDD_ERR_NO_CONVERGENCE = 6,      /* max_iter reached before tol */
+    AMGDD_ERR_DEVICE_TIMEOUT = 7,      /* reserved: a bounded device wait expired */
+    AMGDD_ERR_SINGULAR = 8,            /* coarsest matrix is singular */
+    AMGDD_ERR_NOT_ON_DEVICE = 9        /* handle was set up with host_only = 1 */
+} amgdd_status;
+
+/* Input matrix A_0 (HOST pointers, copied by amgdd_setup). */
+typedef struct {
+    int32_t n;              /* rows = columns */
+    int64_t nnz;            /* = rowptr[n] */
+    const int32_t *rowptr;  /* n+1 entries, rowptr[0] = 0, non-decreasing */
+    const int32_t *col;     /* nnz entries in [0,n), ascending within a row */
+    const double *val;      /* nnz entries; positive diagonal required */
+} amgdd_csr;
+
+/* Setup and solve options. amgdd_options_default fills the defaults. */
+typedef struct {
+    double theta;           /* strength threshold (Section 2), default 0.25 */
+    int32_t max_coarse;     /* stop coarsening at n_l <= max_coarse, default 16 */
+    int32_t max_levels;     /* maximum number of levels, default 25 */
+    int32_t n_fac;          /* AlgFAC V(1,1)-cycles per AMG-DD iteration, default 2 */
+    int32_t strict_assumption; /* 1: fail setup when the assumption is violated */
+    int32_t host_only;      /* 1: build hierarchy and maps on the host only, no
+                               device upload (inspection / CPU testing) */
+    int32_t threads;        /* FAC kernel threads per block (0 = default 512) */
+    int32_t reserved[8];
+} amgdd_options;
+
+/* Statistics of a completed setup. */
+#define AMGDD_MAX_LEVELS 40
+typedef struct {
+    int32_t num_levels;
+    int32_t nsub;
+    int32_t n[AMGDD_MAX_LEVELS];        /* n_l */
+    int64_t nnz[AMGDD_MAX_LEVELS];      /* nnz(A_l) */
+    int64_t nnz_P[AMGDD_MAX_LEVELS];    /* nnz(P_l), l < L */
+    int64_t comp_real[AMGDD_MAX_LEVELS];   /* sum_p |D_l^p| */
+    int64_t comp_ghost[AMGDD_MAX_LEVELS];  /* sum_p |Dbar_l^p \ D_l^p| */
+    int64_t comp_nnz_real[AMGDD_MAX_LEVELS]; /* sum_p nnz of A_l rows of D_l^p */
+    int64_t comp_nnz_A[AMGDD_MAX_LEVELS];  /* stored local A_l entries (real + ghost rows) */
+    int64_t comp_nnz_P[AMGDD_MAX_LEVELS];  /* stored local P_l entries */
+    int64_t comp_nnz_R[AMGDD_MAX_LEVELS];  /* stored local R_l entries */
+    double operator_complexity;         /* sum_l nnz(A_l) / nnz(A_0) */
+    double grid_complexity;             /* sum_l n_l / n_0 */
+    double composite_overhead;          /* Section 6.1 definition */
+    int64_t assumption_violations;      /* grid-level pairs that break the assumption */
+    int64_t device_bytes;               /* device memory held by the handle */
+    double setup_seconds;
+} amgdd_setup_stats;
+
+/* Per-solve report. history: caller-provided HOST buffer of max_iter+1
+ * doubles (or NULL); history[k] = ||b - A x_k|| / ||b|| (||r_0|| if b = 0). */
+typedef struct {
+    int32_t iterations;
+    int32_t converged;
+    double final_relres;
+    double *history;
+    double seconds;         /* host wall time of the solve call */
+    int64_t kernel_launches;/* kernels launched by the call */
+} amgdd_solve_info;
+
+amgdd_status amgdd_options_default(amgdd_options *opts);
+
+/* Box partition helper (the paper partitions with METIS, Section 6; boxes
+ * stand in): unknown (i,j,k) of an nx*ny*nz lexicographic grid (i fastest) goes
+ * to box (i/bx, j/by, k/bz), boxes numbered lexicographically. part: HOST,
+ * nx*ny*nz entries. *nsub receives the number of boxes. nz = bz = 1 for 2D. */
+amgdd_status amgdd_box_partition(int32_t nx, int32_t ny, int32_t nz, int32_t bx, int32_t by,
+                                 int32_t bz, int32_t *part, int32_t *nsub);
+
+/* Setup (Sections 2 and 3): classical AMG hierarchy of A (strength, Ruge-
+ * Stueben first-pass C/F splitting, direct interpolation P_l, R_l = P_l^T,
+ * Galerkin A_{l+1} = R_l A_l P_l), then the composite grid of every subdomain
+ * p: D_0 = points within distance padding[0] of {i : part[i] = p} in graph(A_0),
+ * D_{l+1} = points within padding[l+1] of the C points of D_l in graph(A_{l+1}),
+ * the coarsest level whole, plus one ghost layer Dbar_l (eq. (1)).
+ *   A       : HOST CSR, copied; must be symmetric with a positive diagonal.
+ *   part    : HOST, A->n entries in [0, nsub); every subdomain non-empty.
+ *   padding : HOST, npadding entries eta_0..; the last value repeats for
+ *             deeper levels (npadding >= 1).
+ *   stream  : stream for the upload (ignored when opts->host_only).
+ *   out     : receives the handle (NULL on failure).
+ * Errors: INVALID_ARG, NOT_SYMMETRIC, SINGULAR, HIERARCHY_ASSUMPTION (only with
+ * opts->strict_assumption), OOM, CUDA. */
+amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub,
+                         const int32_t *padding, int32_t npadding, const amgdd_options *opts,
+                         void *stream, amgdd_handle *out);
+
+/* Frees host and device memory of the handle (after synchronising its last
+ * stream). NULL is accepted. */
+void amgdd_destroy(amgdd_handle h);
+
+const char *amgdd_last_error(amgdd_handle h);
+
+amgdd_status amgdd_get_stats(amgdd_handle h, amgdd_setup_stats *stats);
+
+/* Composite-grid index map of subdomain `sub` on `level` (Section 3), local
+ * order: owned points of D_l ascending, other real points ascending, ghost
+ * points ascending. global_idx / kind: HOST buffers of at least *count entries;
+ * with global_idx == NULL only *count = |Dbar_l| is returned.
+ * kind: 0 owned, 1 real (not owned), 2 ghost. */
+amgdd_status amgdd_get_maps(amgdd_handle h, int32_t sub, int32_t level, int32_t *global_idx,
+                            uint8_t *kind, int32_t *count);
+
+/* Host copy of a hierarchy operator. which: 0 = A_l, 1 = P_l, 2 = R_l.
+ * With rowptr == NULL only rows/cols/nnz are returned. Buffers: HOST,
+ * rowptr rows+1 (int64), col nnz, val nnz. */
+amgdd_status amgdd_get_operator(amgdd_handle h, int32_t level, int32_t which, int32_t *rows,
+                                int32_t *cols, int64_t *nnz, int64_t *rowptr, int32_t *col,
+                                double *val);
+
+/* C/F flags (1 = C) of level l < L and 1/l1 row norms of level l (HOST, n_l). */
+amgdd_status amgdd_get_cf(amgdd_handle h, int32_t level, int32_t *cf, double *l1inv);
+
+/* Row-major explicit inverse of the coarsest matrix (HOST, n_L*n_L). */
+amgdd_status amgdd_get_coarse_inverse(amgdd_handle h, double *ainv);
+
+/* ---- solve phase (device pointers, stream-ordered) ---------------------- */
+
+/* Algorithm 2, step 1: r = b - A_0 x on all n rows; *nrm2 (HOST, may be NULL)
+ * receives ||r||_2^2 (order of the reduction is fixed, not sequential).
+ * b, x, r: DEVICE, n doubles each. */
+amgdd_status amgdd_residual(amgdd_handle h, const double *b, const double *x, double *r,
+                            double *nrm2, void *stream);
+
+/* Algorithm 2, step 2: r_{l+1} = R_l r_l for all l. r_all: DEVICE buffer of
+ * sum_l n_l doubles, levels back to back; level 0 is the input. */
+amgdd_status amgdd_restrict(amgdd_handle h, double *r_all, void *stream);
+
+/* Algorithm 2, steps 3-5 in one launch: every composite grid gathers its
+ * right-hand sides f_l = r_l on D_l, runs n_fac AlgFAC V(1,1)-cycles
+ * (Algorithm 4) and adds u_0 on its owned points into x.
+ * r_all: DEVICE (as amgdd_restrict); x: DEVICE, n doubles, updated in place. */
+amgdd_status amgdd_fac(amgdd_handle h, const double *r_all, double *x, void *stream);
+
+/* After amgdd_fac: u_l on Dbar_l and f_l on D_l (zero at ghost points) of one
+ * composite grid, in the amgdd_get_maps order. u, f: HOST, |Dbar_l| each. */
+amgdd_status amgdd_get_fac_state(amgdd_handle h, int32_t sub, int32_t level, double *u, double *f);
+
+/* One AMG-DD iteration (Algorithm 2): residual, restriction, AlgFAC on every
+ * composite grid, owned corrections added into x. b, x: DEVICE, n doubles. */
+amgdd_status amgdd_iterate(amgdd_handle h, const double *b, double *x, void *stream);
+
+/* AMG-DD solver: iterate until ||b - A x|| / ||b|| <= tol or max_iter
+ * iterations. x holds x_0 on entry and the last iterate on exit (also on
+ * NO_CONVERGENCE). b, x: DEVICE. info may be NULL. */
+amgdd_status amgdd_solve(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                         void *stream, amgdd_solve_info *info);
+
+/* One AMG V(1,1)-cycle (Algorithm 1) with CF l1-Jacobi on the same hierarchy,
+ * applied in place to x with right-hand side b. b, x: DEVICE. */
+amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream);
+
+/* V-cycle solver on the same hierarchy, same stopping rule as amgdd_solve. */
+amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double tol,
+                              int32_t max_iter, void *stream, amgdd_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGDD_H */

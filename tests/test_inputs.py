@@ -1,0 +1,69 @@
+"""Pins of the synthetic problem generators (shared by oracle and library)."""
+import numpy as np
+import scipy.sparse as sp
+
+import amgdd_inputs as I
+
+
+def _mat(rp, ci, v):
+    return sp.csr_matrix((v, ci, rp))
+
+
+def test_poisson_sizes_and_exact_symmetry():
+    rp, ci, v = I.poisson2d(64, 64)
+    assert len(rp) - 1 == 4096 and len(ci) == 20224
+    rp, ci, v = I.poisson3d(12, 10, 8)
+    A = _mat(rp, ci, v)
+    assert (A - A.T).count_nonzero() == 0
+    for i in range(A.shape[0]):  # ascending unique columns
+        row = ci[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(row) > 0)
+
+
+def test_dirichlet_laplacian_eigenpairs_2d():
+    # lambda_ij = 4 - 2cos(i pi/(n+1)) - 2cos(j pi/(m+1)), v = sin (x) sin
+    nx, ny = 9, 7
+    A = _mat(*I.poisson2d(nx, ny))
+    for (a, b) in [(1, 1), (2, 3), (9, 7), (5, 1)]:
+        x = np.sin(a * np.pi * np.arange(1, nx + 1) / (nx + 1))
+        y = np.sin(b * np.pi * np.arange(1, ny + 1) / (ny + 1))
+        vec = np.outer(y, x).reshape(-1)  # idx = i + nx*j
+        lam = 4 - 2 * np.cos(a * np.pi / (nx + 1)) - 2 * np.cos(b * np.pi / (ny + 1))
+        assert np.allclose(A @ vec, lam * vec, rtol=0, atol=1e-13)
+
+
+def test_dirichlet_laplacian_eigenpairs_3d():
+    nx, ny, nz = 6, 5, 4
+    A = _mat(*I.poisson3d(nx, ny, nz))
+    for (a, b, c) in [(1, 1, 1), (2, 5, 3), (6, 1, 4)]:
+        x = np.sin(a * np.pi * np.arange(1, nx + 1) / (nx + 1))
+        y = np.sin(b * np.pi * np.arange(1, ny + 1) / (ny + 1))
+        z = np.sin(c * np.pi * np.arange(1, nz + 1) / (nz + 1))
+        vec = np.einsum("k,j,i->kji", z, y, x).reshape(-1)
+        lam = (6 - 2 * np.cos(a * np.pi / (nx + 1)) - 2 * np.cos(b * np.pi / (ny + 1))
+               - 2 * np.cos(c * np.pi / (nz + 1)))
+        assert np.allclose(A @ vec, lam * vec, rtol=0, atol=1e-13)
+
+
+def test_variable_coefficient_reduces_and_harmonic_mean():
+    k = np.full((3, 4, 5), 2.5)
+    A = _mat(*I.diffusion3d(k))
+    B = _mat(*I.poisson3d(5, 4, 3))
+    assert abs(A - 2.5 * B).max() < 1e-14
+    k = np.ones((1, 1, 2))
+    k[0, 0, 1] = 3.0
+    A = _mat(*I.diffusion3d(k)).toarray()
+    h = 2 * 1 * 3 / 4.0
+    assert np.isclose(A[0, 1], -h) and np.isclose(A[1, 0], -h)
+    assert np.isclose(A[0, 0], 5 * 1.0 + h) and np.isclose(A[1, 1], 5 * 3.0 + h)
+
+
+def test_box_partition_and_rhs_seed():
+    part, nsub = I.box_partition((64, 64), (16, 16))
+    assert nsub == 16 and np.all(np.bincount(part) == 256)
+    assert part[0] == 0 and part[16] == 1 and part[64 * 16] == 4
+    part3, ns3 = I.box_partition((32, 32, 32), (16, 16, 16))
+    assert ns3 == 8 and part3[32 * 32 * 16] == 4
+    b0 = I.uniform_rhs(1000, 0)
+    assert np.array_equal(b0, np.random.default_rng(0).uniform(-1, 1, 1000))
+    assert b0.min() >= -1 and b0.max() <= 1

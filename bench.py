@@ -1,0 +1,382 @@
+"""Benchmark: milliseconds to a 1e-8 relative residual, AMG-DD vs the plain
+V-cycle on the same hierarchy, one GB300 per process.
+
+Workload: 3D 7-point Poisson on a 128^3 interior grid (2,097,152 unknowns,
+Dirichlet), b ~ U[-1,1] (seed 0), x0 = 0, 512 box subdomains of 16^3,
+padding 2 on every level, 2 AlgFAC V(1,1)-cycles per AMG-DD iteration, FP64.
+One step = one AMG-DD solve to 1e-8 (residual, restriction, composite-grid
+FAC cycles and owned corrections, repeated until converged). The inputs
+(7.1 GB of composite-grid operators, 183 MB fine matrix) exceed the 126 MB L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`--impl reference` times the CPU oracle (plain C, all host cores) on the
+same workload: every step is one AMG-DD iteration, scaled by the number of
+iterations to 1e-8.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import amgdd_inputs as I  # noqa: E402
+
+WORKLOAD = "poisson3d_128"
+METRIC = "ms to 1e-8 rel. residual & HBM GB/s: AMG-DD vs plain V-cycle, 1 GB300"
+TOL = 1e-8
+
+
+def _config(w):
+    return {
+        "workload": "3D 7-point Poisson 128^3 (N=2,097,152), 512 subdomains of 16^3, padding 2, "
+                    "2 AlgFAC V(1,1) per iteration, FP64, b~U[-1,1] seed 0, x0=0",
+        "n": int(len(w["rowptr"]) - 1), "nnz": int(len(w["col"])), "nsub": int(w["nsub"]),
+        "padding": int(w["padding"]), "n_fac": int(w["n_fac"]), "tol": TOL,
+        "l2_policy": "inputs larger than L2 (composite operators 7 GB, fine matrix 183 MB)",
+    }
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 peak of a GB300: 1.25 TFLOP/s nominal dense (2 DFMA per SM per clock at
+# 2.07 GHz boost on 152 SMs is 1.26 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_fac_bytes(st, nfac):
+    """Bytes one all-grids FAC launch must move (operators once per use).
+
+    A local operator entry is 12 bytes (FP64 value + int32 column), a row adds
+    its 2-byte length. Per cycle and level l < L: the real rows of A_l are read
+    by the pre- and post-smoothing sweeps and every stored row of A_l by
+    s_l + A_l t_l; P_l and R_l are read once; from the second cycle the real
+    rows of A_{l+1} are read once more for the coarse residual recomputation.
+    Vectors: 8 bytes x 8 vector touches per composite point per level visit.
+    """
+    L = st.num_levels - 1
+    tot = 0.0
+    for c in range(1, nfac + 1):
+        for l in range(L):
+            a_all = 12.0 * st.comp_nnz_A[l] + 2.0 * (st.comp_real[l] + st.comp_ghost[l])
+            a_real = 12.0 * st.comp_nnz_real[l] + 2.0 * st.comp_real[l]
+            tot += 2 * a_real + a_all
+            tot += 12.0 * st.comp_nnz_P[l] + 12.0 * st.comp_nnz_R[l]
+            if c > 1:
+                tot += 12.0 * st.comp_nnz_real[l + 1] + 2.0 * st.comp_real[l + 1]
+            tot += 8.0 * 8 * (st.comp_real[l] + st.comp_ghost[l])
+    return tot
+
+
+def algorithmic_fac_flops(st, nfac):
+    """FP64 flops of one FAC launch: 2 per stored operator entry visited."""
+    L = st.num_levels - 1
+    fma = 0.0
+    for c in range(1, nfac + 1):
+        for l in range(L):
+            fma += 2 * st.comp_nnz_real[l] + st.comp_nnz_A[l] + st.comp_nnz_P[l] + st.comp_nnz_R[l]
+            if c > 1:
+                fma += st.comp_nnz_real[l + 1]
+        fma += st.nsub * float(st.n[L]) ** 2
+    return 2.0 * fma
+
+
+def algorithmic_solve_bytes(st, fac_bytes, iters):
+    """Per AMG-DD iteration: residual (A_0 + 3 vectors), restriction chain
+    (R_l + 2 vectors), the FAC launch; plus one final residual."""
+    L = st.num_levels - 1
+    res = 12.0 * st.nnz[0] + 4.0 * st.n[0] + 24.0 * st.n[0]
+    rst = sum(12.0 * st.nnz_P[l] + 4.0 * st.n[l + 1] + 8.0 * (st.n[l] + st.n[l + 1]) for l in range(L))
+    return iters * (res + rst + fac_bytes) + res
+
+
+def vcycle_bytes(st, iters):
+    """Per V(1,1)-cycle: A_l read by 4 half-sweeps (C, F, F, C: two full
+    sweeps), the residual and the level-0 residual check; P_l, R_l once."""
+    L = st.num_levels - 1
+    b = 0.0
+    for l in range(L):
+        b += 3 * (12.0 * st.nnz[l] + 4.0 * st.n[l]) + 2 * 12.0 * st.nnz_P[l] + 10 * 8.0 * st.n[l]
+    b += 12.0 * st.nnz[0] + 28.0 * st.n[0]
+    return iters * b
+
+
+def run_reference(args, w):
+    """CPU oracle arm: each step is one AMG-DD iteration on all host cores."""
+    from oracle import Oracle
+    cores = os.cpu_count()
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"])
+    b = w["b"]
+    # iterations to 1e-8 (identical on every implementation of the same arithmetic)
+    t0 = time.perf_counter()
+    _, hist = o.amgdd_solve(b, w["n_fac"], tol=TOL, maxit=100)
+    full = (time.perf_counter() - t0) * 1e3
+    iters = len(hist) - 1
+    x = np.zeros(o.n)
+    for _ in range(max(0, args.warmup - 1)):
+        x = o.amgdd_iteration(b, x, w["n_fac"])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x = o.amgdd_iteration(b, x, w["n_fac"])
+        times.append((time.perf_counter() - t0) * 1e3)
+    per_iter = statistics.median(times)
+    value = per_iter * iters
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(per_iter, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(w),
+        "iterations": iters, "full_solve_ms": round(full, 1),
+        "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": "one AMG-DD iteration over all 512 composite grids per step "
+                                   "(OpenMP over grids), x %d iterations to 1e-8" % iters},
+        "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def cpu_baseline(w, iters, o_cache={}):
+    """Oracle timed on a bounded sample: one AMG-DD iteration over a subset of
+    composite grids, scaled to all grids and to the iterations to 1e-8."""
+    from oracle import Oracle
+    cores = os.cpu_count()
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"])
+    b = w["b"]
+    nsample = min(w["nsub"], max(2 * cores, 32))
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(w["nsub"], size=nsample, replace=False)).astype(np.int32)
+    o.amgdd_iteration(b, np.zeros(o.n), w["n_fac"], subset=sel[:cores])   # warm caches
+    t0 = time.perf_counter()
+    o.amgdd_iteration(b, np.zeros(o.n), w["n_fac"], subset=sel)
+    t_sample = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = o.residual(b, np.zeros(o.n))
+    o.restrict_all(r)
+    t_global = time.perf_counter() - t0
+    per_iter = t_global + (t_sample - t_global) * w["nsub"] / nsample
+    return {"value": round(per_iter * iters * 1e3, 2), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d composite grids of one AMG-DD iteration (%.2f s), scaled to all grids "
+                      "and %d iterations" % (nsample, w["nsub"], t_sample, iters)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = I.workload(WORKLOAD, seed=0)
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, w)
+        return
+
+    import torch
+    from paper_1906_10575_gb300 import Solver, capi
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+               stream=stream)
+    st = s.stats
+    b = torch.from_numpy(w["b"]).cuda()
+    x = torch.zeros_like(b)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, k):
+        times, infos = [], []
+        for _ in range(k):
+            x.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = fn(b, x, tol=TOL, max_iter=200, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return times, infos
+
+    with torch.cuda.stream(stream):
+        timed(s.solve, args.warmup)
+        barrier()
+        clk = ClockSampler(local)
+        t_dd, i_dd = timed(s.solve, args.steps)
+        clocks = clk.stop()
+        barrier()
+        timed(s.vcycle_solve, args.warmup)
+        t_v, i_v = timed(s.vcycle_solve, args.steps)
+        barrier()
+        # dominant kernel alone: the all-grids FAC launch
+        r_all = torch.zeros(int(s.offsets[-1]), dtype=torch.float64, device="cuda")
+        capi.amgdd_residual(s.h, b, torch.zeros_like(b), r_all[:s.n], stream)
+        capi.amgdd_restrict(s.h, r_all, stream)
+        xf = torch.zeros_like(b)
+        for _ in range(2):
+            capi.amgdd_fac(s.h, r_all, xf, stream)
+        nf = 5
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nf):
+            capi.amgdd_fac(s.h, r_all, xf, stream)
+        e1.record(stream)
+        e1.synchronize()
+        fac_ms = e0.elapsed_time(e1) / nf
+        # end to end through the C ABI with host buffers
+        hb = torch.from_numpy(w["b"]).pin_memory()
+        hx = torch.empty_like(hb).pin_memory()
+        t_e2e = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            db = hb.to("cuda", non_blocking=True)
+            dx = torch.zeros_like(db)
+            s.solve(db, dx, tol=TOL, max_iter=200, stream=stream)
+            hx.copy_(dx, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                t_e2e.append(e0.elapsed_time(e1))
+
+    ms_dd = statistics.median(t_dd)
+    ms_v = statistics.median(t_v)
+    ms_e2e = statistics.median(t_e2e)
+    if dist is not None:
+        tt = torch.tensor([ms_dd, ms_v, ms_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_dd, ms_v, ms_e2e = [float(v) for v in tt.cpu()]
+    it_dd = i_dd[-1]["iterations"]
+    it_v = i_v[-1]["iterations"]
+    hbm, peak_kind = _peaks()
+    fac_b = algorithmic_fac_bytes(st, w["n_fac"])
+    fac_f = algorithmic_fac_flops(st, w["n_fac"])
+    fac_gbs = fac_b / (fac_ms * 1e-3) / 1e9
+    fac_tfs = fac_f / (fac_ms * 1e-3) / 1e12
+    frac_hbm = fac_gbs / hbm
+    frac_alu = fac_tfs / FP64_PEAK_TFLOPS
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": round(fac_tfs, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(frac_alu, 4),
+                "peak_source": "nominal FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz)"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(fac_gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(frac_hbm, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
+    roof.update({"kernel": "k_fac_all_grids", "traffic": None, "ms_per_launch": round(fac_ms, 3),
+                 "algorithmic_bytes": fac_b, "algorithmic_flops": fac_f,
+                 "hbm_frac_of_measured": round(frac_hbm, 4), "fp64_frac_of_nominal": round(frac_alu, 4)})
+    dd_bytes = algorithmic_solve_bytes(st, fac_b, it_dd)
+    v_bytes = vcycle_bytes(st, it_v)
+    launches = int(i_dd[-1]["kernel_launches"])
+    line = {
+        "metric": METRIC, "value": round(ms_dd, 3), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_dd, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(w),
+        "iterations": it_dd, "final_relres": i_dd[-1]["final_relres"],
+        "gbs": round(dd_bytes / (ms_dd * 1e-3) / 1e9, 1),
+        "vcycle": {"ms": round(ms_v, 3), "iterations": it_v, "final_relres": i_v[-1]["final_relres"],
+                   "gbs": round(v_bytes / (ms_v * 1e-3) / 1e9, 1),
+                   "kernel_launches": int(i_v[-1]["kernel_launches"])},
+        "amgdd_over_vcycle_time": round(ms_dd / ms_v, 3),
+        "composite_overhead": round(st.composite_overhead, 3),
+        "operator_complexity": round(st.operator_complexity, 3),
+        "setup_s": round(st.setup_seconds, 2),
+        "roofline": roof,
+        "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
+        "e2e": {"value": round(ms_e2e, 3), "unit": "ms", "h2d_bytes_per_step": 8 * s.n,
+                "d2h_bytes_per_step": 8 * s.n},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, it_dd)
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -64,7 +64,9 @@ typedef struct {
     int32_t n_fac;          /* AlgFAC V(1,1)-cycles per AMG-DD iteration, default 2 */
     int32_t strict_assumption; /* 1: fail setup when the assumption is violated */
     int32_t host_only;      /* 1: build hierarchy and maps on the host only, no
-                               device upload (inspection / CPU testing) */
+                               device upload (inspection / CPU testing);
+                               2: also build and range-check the device layouts,
+                               still without touching the device */
     int32_t threads;        /* FAC kernel threads per block (0 = default 512) */
     int32_t reserved[8];
 } amgdd_options;

@@ -1,0 +1,114 @@
+// Internal host-side structures of the AMG-DD library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace amgdd {
+
+// Host CSR: ascending unique columns per row.
+struct Csr {
+    int32_t rows = 0, cols = 0;
+    std::vector<int64_t> ptr;   // rows+1
+    std::vector<int32_t> idx;
+    std::vector<double> val;
+    int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+// One level of the classical AMG hierarchy (Section 2).
+struct HLevel {
+    Csr A;                        // A_l
+    Csr P;                        // P_l : n_l x n_{l+1} (l < L)
+    Csr R;                        // R_l = P_l^T (l < L)
+    std::vector<uint8_t> isC;     // l < L: 1 for C points
+    std::vector<int32_t> coarse;  // l < L: coarse index of a C point, -1 otherwise
+    std::vector<double> l1inv;    // 1 / sum_j |a_ij|
+};
+
+struct Hierarchy {
+    std::vector<HLevel> lv;       // levels 0..L
+    std::vector<double> ainv;     // row-major inverse of A_L
+    int L() const { return (int)lv.size() - 1; }
+};
+
+struct HierarchyParams {
+    double theta = 0.25;
+    int max_coarse = 16;
+    int max_levels = 25;
+};
+
+// Returns an empty string on success, else the reason.
+std::string build_hierarchy(const Csr &A0, const HierarchyParams &prm, Hierarchy &H, int &status);
+
+// Composite grid of one subdomain on one level (Section 3, eq. (1)); all sets
+// hold ascending global indices of the level.
+struct CompLevel {
+    std::vector<int32_t> owned;   // Omega_l^p
+    std::vector<int32_t> real;    // D_l^p
+    std::vector<int32_t> ghost;   // Dbar_l^p \ D_l^p
+};
+
+struct Composite {
+    int nsub = 0, nlev = 0;
+    std::vector<CompLevel> g;     // [p * nlev + l]
+    int64_t violations = 0;
+    const CompLevel &at(int p, int l) const { return g[(size_t)p * nlev + l]; }
+    CompLevel &at(int p, int l) { return g[(size_t)p * nlev + l]; }
+};
+
+void build_composite(const Hierarchy &H, const int32_t *part, int nsub,
+                     const std::vector<int> &eta, Composite &C, int nthreads);
+
+// ---------------------------------------------------------------------------
+// Device-side layouts (filled on the host, uploaded as flat arrays).
+//
+// SELL-32: rows grouped in slices of 32 consecutive (device-order) rows; the
+// k-th entry of row 32*s + lane is stored at soff[s] + 32*k + lane, entries of
+// a row in ascending column order of the level's global numbering. rlen holds
+// each row's length; a slice's width is (soff[s+1]-soff[s])/32.
+struct Sell {
+    int32_t rows = 0;
+    std::vector<int64_t> soff;    // slices+1
+    std::vector<uint16_t> rlen;   // rows
+    std::vector<int32_t> col;
+    std::vector<double> val;
+};
+
+// Row order [C rows ascending | F rows ascending] of a global level; rowid maps
+// a device row to the level index.
+struct GlobalLevelDev {
+    Sell A;                       // rows in C|F order (all rows for l = L)
+    std::vector<int32_t> rowid;   // device row -> level index
+    int32_t nC = 0;
+    Sell P;                       // natural row order (l < L)
+    Sell R;                       // natural row order (l < L)
+};
+
+struct FacLayout {
+    int nlev = 0, nsub = 0;
+    std::vector<FacLevelDesc> desc;       // [p * nlev + l]
+    std::vector<int32_t> gmap;            // local -> level index
+    std::vector<double> l1inv;            // per row (real rows used)
+    std::vector<uint16_t> rlenA, rlenP, rlenR;  // per row; R stored on its row level
+    std::vector<int64_t> soffA, soffP, soffR;   // per slice (+1 sentinel per grid-level)
+    std::vector<int32_t> colA, colP, colR;
+    std::vector<double> valA, valP, valR;
+    std::vector<int32_t> owned;           // level-0 local indices of owned points
+    std::vector<int64_t> owned0;          // per grid offset into owned (nsub+1)
+    std::vector<int32_t> order;           // grids in launch order (largest first)
+    std::vector<int64_t> work;            // per grid estimated FMA count per cycle
+    // local device order -> position in the map order (owned, real, ghost)
+    std::vector<int32_t> dev2map;         // per row
+    int64_t rows_total = 0, slices_total = 0;
+};
+
+void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads);
+void build_global_dev(const Hierarchy &H, std::vector<GlobalLevelDev> &G);
+
+// Range checks of every index the kernels will dereference; empty if valid.
+std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDev> &G, const FacLayout &F);
+
+}  // namespace amgdd

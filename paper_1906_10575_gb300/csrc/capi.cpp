@@ -1,0 +1,732 @@
+// C ABI of the AMG-DD solve-phase library (declared in include/amgdd.h).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/amgdd.h"
+#include "amgdd_internal.hpp"
+
+using namespace amgdd;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct DevLevel {             // device copy of one global level
+    SellView A{}, P{}, R{};
+    int64_t n = 0;
+    int64_t nC = 0;
+    const double *l1inv = nullptr;
+    double *u = nullptr, *f = nullptr, *d = nullptr;   // V-cycle vectors (level >= 1: u, f)
+};
+
+}  // namespace
+
+struct amgdd_handle_s {
+    std::string err;
+    amgdd_options opt{};
+    Hierarchy H;
+    Composite C;
+    std::vector<FacLevelDesc> desc;     // host copy of the FAC descriptors
+    std::vector<int32_t> dev2map;       // device order -> map order, per row
+    std::vector<int64_t> level_off;     // offsets of the levels in r_all
+    amgdd_setup_stats stats{};
+    bool on_device = false;
+    // device memory
+    std::vector<void *> allocs;
+    int64_t dev_bytes = 0;
+    std::vector<DevLevel> lev;
+    const double *ainv = nullptr;
+    int nL = 0;
+    FacParams fac{};
+    double *r_all = nullptr;            // sum_l n_l
+    double *res = nullptr;              // n_0 scratch
+    double *partial = nullptr;          // reduction partials
+    double *scal = nullptr;             // device scalars
+    double *h_scal = nullptr;           // pinned host scalars
+    int nred = 0;                       // reduction blocks
+    int threads = 512;
+    int64_t launches = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+amgdd_status fail(amgdd_handle h, amgdd_status st, const std::string &msg)
+{
+    if (h) h->err = msg;
+    g_last_error = msg;
+    return st;
+}
+
+amgdd_status cuda_fail(amgdd_handle h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? AMGDD_ERR_OOM : AMGDD_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                                  \
+    do {                                                                \
+        cudaError_t _e = (expr);                                        \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, what);           \
+    } while (0)
+
+template <class T>
+cudaError_t upload(amgdd_handle h, const std::vector<T> &v, T **out, cudaStream_t st)
+{
+    *out = nullptr;
+    const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(p);
+    h->dev_bytes += (int64_t)bytes;
+    if (!v.empty()) {
+        e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    *out = static_cast<T *>(p);
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t alloc(amgdd_handle h, size_t count, T **out)
+{
+    *out = nullptr;
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(p);
+    h->dev_bytes += (int64_t)bytes;
+    *out = static_cast<T *>(p);
+    return cudaSuccess;
+}
+
+cudaError_t upload_sell(amgdd_handle h, Sell &S, const std::vector<int32_t> *rowid, SellView &v, cudaStream_t st)
+{
+    int64_t *soff;
+    uint16_t *rlen;
+    int32_t *col, *rid = nullptr;
+    double *val;
+    cudaError_t e;
+    if ((e = upload(h, S.soff, &soff, st)) != cudaSuccess) return e;
+    if ((e = upload(h, S.rlen, &rlen, st)) != cudaSuccess) return e;
+    if ((e = upload(h, S.col, &col, st)) != cudaSuccess) return e;
+    if ((e = upload(h, S.val, &val, st)) != cudaSuccess) return e;
+    if (rowid && (e = upload(h, *rowid, &rid, st)) != cudaSuccess) return e;
+    v.rows = S.rows;
+    v.soff = soff;
+    v.rlen = rlen;
+    v.col = col;
+    v.val = val;
+    v.rowid = rid;
+    return cudaSuccess;
+}
+
+std::string validate(const amgdd_csr *A, const int32_t *part, int32_t nsub, const int32_t *padding,
+                     int32_t npadding, amgdd_status &st)
+{
+    st = AMGDD_ERR_INVALID_ARG;
+    if (!A || !A->rowptr || !A->col || !A->val) return "null matrix pointer";
+    if (A->n <= 0) return "matrix has no rows";
+    if (!part) return "null partition";
+    if (nsub <= 0) return "nsub must be positive";
+    if (!padding || npadding < 1) return "padding needs at least one entry";
+    for (int i = 0; i < npadding; ++i)
+        if (padding[i] < 0) return "padding must be >= 0";
+    const int32_t n = A->n;
+    if (A->rowptr[0] != 0 || (int64_t)A->rowptr[n] != A->nnz) return "rowptr[0] must be 0 and rowptr[n] = nnz";
+    for (int32_t i = 0; i < n; ++i) {
+        if (A->rowptr[i + 1] < A->rowptr[i]) return "rowptr is not non-decreasing";
+        bool diag = false;
+        for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
+            const int32_t j = A->col[k];
+            if (j < 0 || j >= n) return "column index out of range in row " + std::to_string(i);
+            if (k > A->rowptr[i] && A->col[k - 1] >= j) return "columns not strictly ascending in row " + std::to_string(i);
+            if (!std::isfinite(A->val[k])) return "non-finite value in row " + std::to_string(i);
+            if (j == i) {
+                diag = true;
+                if (!(A->val[k] > 0.0)) return "non-positive diagonal in row " + std::to_string(i);
+            }
+        }
+        if (!diag) return "missing diagonal in row " + std::to_string(i);
+    }
+    std::vector<int64_t> cnt((size_t)nsub, 0);
+    for (int32_t i = 0; i < n; ++i) {
+        if (part[i] < 0 || part[i] >= nsub) return "part[" + std::to_string(i) + "] out of range";
+        cnt[part[i]]++;
+    }
+    for (int32_t p = 0; p < nsub; ++p)
+        if (cnt[p] == 0) return "subdomain " + std::to_string(p) + " owns no unknowns";
+    // symmetry: every (i, j) has a matching (j, i) of nearly equal value
+    st = AMGDD_ERR_NOT_SYMMETRIC;
+    std::vector<int32_t> pos(A->rowptr, A->rowptr + n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
+            const int32_t j = A->col[k];
+            if (j < i) continue;
+            // find (j, i) by scanning row j from its cursor
+            int32_t q = pos[j];
+            while (q < A->rowptr[j + 1] && A->col[q] < i) ++q;
+            if (q >= A->rowptr[j + 1] || A->col[q] != i)
+                return "entry (" + std::to_string(i) + "," + std::to_string(j) + ") has no transpose";
+            const double a = A->val[k], b = A->val[q];
+            if (std::fabs(a - b) > 1e-12 * std::max(std::fabs(a), std::fabs(b)))
+                return "values (" + std::to_string(i) + "," + std::to_string(j) + ") not symmetric";
+        }
+    st = AMGDD_OK;
+    return "";
+}
+
+int host_threads()
+{
+    unsigned t = std::thread::hardware_concurrency();
+    return t == 0 ? 4 : (int)std::min(t, 64u);
+}
+
+amgdd_status require_device(amgdd_handle h)
+{
+    if (!h) return fail(nullptr, AMGDD_ERR_INVALID_ARG, "null handle");
+    if (!h->on_device) return fail(h, AMGDD_ERR_NOT_ON_DEVICE, "handle was set up with host_only");
+    return AMGDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amgdd_status amgdd_options_default(amgdd_options *o)
+{
+    if (!o) return fail(nullptr, AMGDD_ERR_INVALID_ARG, "null options");
+    std::memset(o, 0, sizeof *o);
+    o->theta = 0.25;
+    o->max_coarse = 16;
+    o->max_levels = 25;
+    o->n_fac = 2;
+    o->strict_assumption = 0;
+    o->host_only = 0;
+    o->threads = 0;
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_box_partition(int32_t nx, int32_t ny, int32_t nz, int32_t bx, int32_t by, int32_t bz,
+                                 int32_t *part, int32_t *nsub)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0 || bx <= 0 || by <= 0 || bz <= 0 || !part)
+        return fail(nullptr, AMGDD_ERR_INVALID_ARG, "box partition: sizes must be positive");
+    const int64_t mx = (nx + bx - 1) / bx, my = (ny + by - 1) / by, mz = (nz + bz - 1) / bz;
+    if (mx * my * mz > INT32_MAX) return fail(nullptr, AMGDD_ERR_INVALID_ARG, "too many boxes");
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i)
+                part[i + nx * (j + ny * k)] = (int32_t)((i / bx) + mx * ((j / by) + my * (k / bz)));
+    if (nsub) *nsub = (int32_t)(mx * my * mz);
+    return AMGDD_OK;
+}
+
+const char *amgdd_last_error(amgdd_handle h)
+{
+    if (h) return h->err.c_str();
+    return g_last_error.c_str();
+}
+
+void amgdd_destroy(amgdd_handle h)
+{
+    if (!h) return;
+    if (h->on_device) {
+        cudaStreamSynchronize(h->last_stream);
+        for (void *p : h->allocs) cudaFree(p);
+        if (h->h_scal) cudaFreeHost(h->h_scal);
+    }
+    delete h;
+}
+
+amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, const int32_t *padding,
+                         int32_t npadding, const amgdd_options *opts, void *stream, amgdd_handle *out)
+{
+    if (!out) return fail(nullptr, AMGDD_ERR_INVALID_ARG, "null output handle pointer");
+    *out = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
+    amgdd_status st;
+    std::string why = validate(A, part, nsub, padding, npadding, st);
+    if (st != AMGDD_OK) return fail(nullptr, st, why);
+    amgdd_handle h = new (std::nothrow) amgdd_handle_s();
+    if (!h) return fail(nullptr, AMGDD_ERR_OOM, "host allocation failed");
+    if (opts) h->opt = *opts;
+    else amgdd_options_default(&h->opt);
+    if (h->opt.n_fac < 1 || h->opt.max_levels < 1 || h->opt.max_coarse < 1 || !(h->opt.theta > 0.0) ||
+        !(h->opt.theta <= 1.0)) {
+        delete h;
+        return fail(nullptr, AMGDD_ERR_INVALID_ARG, "options out of range");
+    }
+    h->threads = h->opt.threads > 0 ? h->opt.threads : 512;
+    if (h->threads % 32 != 0 || h->threads > 512) {
+        delete h;
+        return fail(nullptr, AMGDD_ERR_INVALID_ARG, "threads must be a multiple of 32 up to 512");
+    }
+    try {
+        Csr A0;
+        A0.rows = A0.cols = A->n;
+        A0.ptr.assign(A->rowptr, A->rowptr + A->n + 1);
+        A0.idx.assign(A->col, A->col + A->nnz);
+        A0.val.assign(A->val, A->val + A->nnz);
+        HierarchyParams prm;
+        prm.theta = h->opt.theta;
+        prm.max_coarse = h->opt.max_coarse;
+        prm.max_levels = std::min(h->opt.max_levels, (int32_t)AMGDD_MAX_LEVELS);
+        int hst = 0;
+        why = build_hierarchy(A0, prm, h->H, hst);
+        if (hst != 0) {
+            delete h;
+            return fail(nullptr, hst == 1 ? AMGDD_ERR_SINGULAR : AMGDD_ERR_INVALID_ARG, why);
+        }
+        const int nlev = (int)h->H.lv.size();
+        std::vector<int> eta((size_t)nlev);
+        for (int l = 0; l < nlev; ++l) eta[l] = padding[std::min(l, npadding - 1)];
+        const int nth = host_threads();
+        build_composite(h->H, part, nsub, eta, h->C, nth);
+        if (h->opt.strict_assumption && h->C.violations > 0) {
+            delete h;
+            return fail(nullptr, AMGDD_ERR_HIERARCHY_ASSUMPTION,
+                        "composite grids break the connectivity assumption");
+        }
+        // statistics
+        amgdd_setup_stats &S = h->stats;
+        S.num_levels = nlev;
+        S.nsub = nsub;
+        double nnz_sum = 0, n_sum = 0, real_nnz = 0;
+        for (int l = 0; l < nlev; ++l) {
+            S.n[l] = h->H.lv[l].A.rows;
+            S.nnz[l] = h->H.lv[l].A.nnz();
+            S.nnz_P[l] = l + 1 < nlev ? h->H.lv[l].P.nnz() : 0;
+            nnz_sum += (double)S.nnz[l];
+            n_sum += S.n[l];
+            const Csr &Al = h->H.lv[l].A;
+            for (int p = 0; p < nsub; ++p) {
+                const CompLevel &cl = h->C.at(p, l);
+                S.comp_real[l] += (int64_t)cl.real.size();
+                S.comp_ghost[l] += (int64_t)cl.ghost.size();
+                for (int32_t i : cl.real) S.comp_nnz_real[l] += Al.ptr[i + 1] - Al.ptr[i];
+            }
+            real_nnz += (double)S.comp_nnz_real[l];
+        }
+        S.operator_complexity = nnz_sum / (double)S.nnz[0];
+        S.grid_complexity = n_sum / (double)S.n[0];
+        S.composite_overhead = real_nnz / nnz_sum;
+        S.assumption_violations = h->C.violations;
+        h->level_off.assign((size_t)nlev + 1, 0);
+        for (int l = 0; l < nlev; ++l) h->level_off[l + 1] = h->level_off[l] + S.n[l];
+
+        if (h->opt.host_only != 1) {
+            cudaStream_t st_ = (cudaStream_t)stream;
+            h->last_stream = st_;
+            FacLayout F;
+            build_fac_layout(h->H, h->C, F, nth);
+            // stored entries of the local operators (padding excluded)
+            for (int p = 0; p < nsub; ++p)
+                for (int l = 0; l < nlev; ++l) {
+                    const FacLevelDesc &d = F.desc[(size_t)p * nlev + l];
+                    for (int32_t r = 0; r < d.nBar; ++r) {
+                        S.comp_nnz_A[l] += F.rlenA[d.row0 + r];
+                        S.comp_nnz_P[l] += F.rlenP[d.row0 + r];
+                        if (l > 0) S.comp_nnz_R[l - 1] += F.rlenR[d.row0 + r];
+                    }
+                }
+            std::vector<GlobalLevelDev> G;
+            build_global_dev(h->H, G);
+            const std::string bad = validate_layouts(h->H, G, F);
+            if (!bad.empty()) {
+                delete h;
+                return fail(nullptr, AMGDD_ERR_INVALID_ARG, "internal layout check failed: " + bad);
+            }
+            if (h->opt.host_only == 2) goto done;
+            auto bail = [&](cudaError_t e, const char *what) {
+                amgdd_status s2 = cuda_fail(nullptr, e, what);
+                for (void *p : h->allocs) cudaFree(p);
+                h->allocs.clear();
+                delete h;
+                return s2;
+            };
+            cudaError_t e;
+            h->lev.assign((size_t)nlev, DevLevel{});
+            size_t maxn = 0;
+            for (int l = 0; l < nlev; ++l) {
+                DevLevel &D = h->lev[l];
+                D.n = h->H.lv[l].A.rows;
+                D.nC = G[l].nC;
+                maxn = std::max(maxn, (size_t)D.n);
+                if ((e = upload_sell(h, G[l].A, &G[l].rowid, D.A, st_)) != cudaSuccess) return bail(e, "upload A_l");
+                if (l + 1 < nlev) {
+                    if ((e = upload_sell(h, G[l].P, nullptr, D.P, st_)) != cudaSuccess) return bail(e, "upload P_l");
+                    if ((e = upload_sell(h, G[l].R, nullptr, D.R, st_)) != cudaSuccess) return bail(e, "upload R_l");
+                }
+                double *l1;
+                if ((e = upload(h, h->H.lv[l].l1inv, &l1, st_)) != cudaSuccess) return bail(e, "upload l1");
+                D.l1inv = l1;
+                if (l > 0) {
+                    if ((e = alloc(h, (size_t)D.n, &D.u)) != cudaSuccess) return bail(e, "alloc u_l");
+                    if ((e = alloc(h, (size_t)D.n, &D.f)) != cudaSuccess) return bail(e, "alloc f_l");
+                }
+                if ((e = alloc(h, (size_t)D.n, &D.d)) != cudaSuccess) return bail(e, "alloc d_l");
+                // the host copies of the device layout are no longer needed
+                G[l] = GlobalLevelDev();
+            }
+            double *ainv;
+            if ((e = upload(h, h->H.ainv, &ainv, st_)) != cudaSuccess) return bail(e, "upload coarse inverse");
+            h->ainv = ainv;
+            h->nL = h->H.lv.back().A.rows;
+            if ((e = alloc(h, (size_t)h->level_off.back(), &h->r_all)) != cudaSuccess) return bail(e, "alloc r");
+            if ((e = alloc(h, maxn, &h->res)) != cudaSuccess) return bail(e, "alloc res");
+            h->nred = 152 * 8;
+            if ((e = alloc(h, (size_t)h->nred, &h->partial)) != cudaSuccess) return bail(e, "alloc partial");
+            if ((e = alloc(h, 8, &h->scal)) != cudaSuccess) return bail(e, "alloc scalars");
+            if ((e = cudaMallocHost((void **)&h->h_scal, 8 * sizeof(double))) != cudaSuccess)
+                return bail(e, "alloc pinned");
+            // composite-grid layout
+            FacParams &P = h->fac;
+            P.nlev = nlev;
+            P.nsub = nsub;
+            P.nfac = h->opt.n_fac;
+            P.nL = h->nL;
+            FacLevelDesc *dd;
+            int32_t *ord, *gm, *colA, *colP, *colR, *own;
+            double *l1, *vA, *vP, *vR;
+            uint16_t *rA, *rP, *rR;
+            int64_t *sA, *sP, *sR, *o0;
+            if ((e = upload(h, F.desc, &dd, st_)) != cudaSuccess) return bail(e, "upload desc");
+            if ((e = upload(h, F.order, &ord, st_)) != cudaSuccess) return bail(e, "upload order");
+            if ((e = upload(h, F.gmap, &gm, st_)) != cudaSuccess) return bail(e, "upload gmap");
+            if ((e = upload(h, F.l1inv, &l1, st_)) != cudaSuccess) return bail(e, "upload l1inv");
+            if ((e = upload(h, F.rlenA, &rA, st_)) != cudaSuccess) return bail(e, "upload rlenA");
+            if ((e = upload(h, F.rlenP, &rP, st_)) != cudaSuccess) return bail(e, "upload rlenP");
+            if ((e = upload(h, F.rlenR, &rR, st_)) != cudaSuccess) return bail(e, "upload rlenR");
+            if ((e = upload(h, F.soffA, &sA, st_)) != cudaSuccess) return bail(e, "upload soffA");
+            if ((e = upload(h, F.soffP, &sP, st_)) != cudaSuccess) return bail(e, "upload soffP");
+            if ((e = upload(h, F.soffR, &sR, st_)) != cudaSuccess) return bail(e, "upload soffR");
+            if ((e = upload(h, F.colA, &colA, st_)) != cudaSuccess) return bail(e, "upload colA");
+            if ((e = upload(h, F.colP, &colP, st_)) != cudaSuccess) return bail(e, "upload colP");
+            if ((e = upload(h, F.colR, &colR, st_)) != cudaSuccess) return bail(e, "upload colR");
+            if ((e = upload(h, F.valA, &vA, st_)) != cudaSuccess) return bail(e, "upload valA");
+            if ((e = upload(h, F.valP, &vP, st_)) != cudaSuccess) return bail(e, "upload valP");
+            if ((e = upload(h, F.valR, &vR, st_)) != cudaSuccess) return bail(e, "upload valR");
+            if ((e = upload(h, F.owned, &own, st_)) != cudaSuccess) return bail(e, "upload owned");
+            if ((e = upload(h, F.owned0, &o0, st_)) != cudaSuccess) return bail(e, "upload owned0");
+            P.desc = dd;
+            P.order = ord;
+            P.gmap = gm;
+            P.l1inv = l1;
+            P.rlenA = rA; P.rlenP = rP; P.rlenR = rR;
+            P.soffA = sA; P.soffP = sP; P.soffR = sR;
+            P.colA = colA; P.colP = colP; P.colR = colR;
+            P.valA = vA; P.valP = vP; P.valR = vR;
+            P.owned = own;
+            P.owned0 = o0;
+            P.ainv = h->ainv;
+            for (int l = 0; l <= kMaxLevels; ++l) P.level_off[l] = l <= nlev ? h->level_off[l] : 0;
+            double *ws[6];
+            for (int k = 0; k < 6; ++k)
+                if ((e = alloc(h, (size_t)F.rows_total, &ws[k])) != cudaSuccess) return bail(e, "alloc FAC workspace");
+            P.u = ws[0]; P.f = ws[1]; P.t = ws[2]; P.s = ws[3]; P.w = ws[4]; P.d = ws[5];
+            if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "setup upload");
+            h->desc = F.desc;
+            h->dev2map = F.dev2map;
+            h->on_device = true;
+        }
+    done:
+        h->stats.device_bytes = h->dev_bytes;
+    } catch (const std::bad_alloc &) {
+        for (void *p : h->allocs) cudaFree(p);
+        delete h;
+        return fail(nullptr, AMGDD_ERR_OOM, "host allocation failed during setup");
+    }
+    h->stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_get_stats(amgdd_handle h, amgdd_setup_stats *s)
+{
+    if (!h || !s) return fail(h, AMGDD_ERR_INVALID_ARG, "null argument");
+    *s = h->stats;
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_get_maps(amgdd_handle h, int32_t sub, int32_t level, int32_t *global_idx, uint8_t *kind,
+                            int32_t *count)
+{
+    if (!h || !count) return fail(h, AMGDD_ERR_INVALID_ARG, "null argument");
+    if (sub < 0 || sub >= h->C.nsub || level < 0 || level >= h->C.nlev)
+        return fail(h, AMGDD_ERR_INVALID_ARG, "subdomain or level out of range");
+    const CompLevel &cl = h->C.at(sub, level);
+    const int32_t n = (int32_t)(cl.real.size() + cl.ghost.size());
+    *count = n;
+    if (!global_idx) return AMGDD_OK;
+    int32_t o = 0;
+    for (int32_t i : cl.owned) { global_idx[o] = i; if (kind) kind[o] = 0; ++o; }
+    size_t a = 0;
+    for (int32_t i : cl.real) {
+        while (a < cl.owned.size() && cl.owned[a] < i) ++a;
+        if (a < cl.owned.size() && cl.owned[a] == i) continue;
+        global_idx[o] = i;
+        if (kind) kind[o] = 1;
+        ++o;
+    }
+    for (int32_t i : cl.ghost) { global_idx[o] = i; if (kind) kind[o] = 2; ++o; }
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_get_operator(amgdd_handle h, int32_t level, int32_t which, int32_t *rows, int32_t *cols,
+                                int64_t *nnz, int64_t *rowptr, int32_t *col, double *val)
+{
+    if (!h) return fail(h, AMGDD_ERR_INVALID_ARG, "null handle");
+    const int nlev = (int)h->H.lv.size();
+    if (level < 0 || level >= nlev || which < 0 || which > 2 || (which > 0 && level == nlev - 1))
+        return fail(h, AMGDD_ERR_INVALID_ARG, "level/operator out of range");
+    const Csr &M = which == 0 ? h->H.lv[level].A : which == 1 ? h->H.lv[level].P : h->H.lv[level].R;
+    if (rows) *rows = M.rows;
+    if (cols) *cols = M.cols;
+    if (nnz) *nnz = M.nnz();
+    if (rowptr) {
+        std::copy(M.ptr.begin(), M.ptr.end(), rowptr);
+        if (col) std::copy(M.idx.begin(), M.idx.end(), col);
+        if (val) std::copy(M.val.begin(), M.val.end(), val);
+    }
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_get_cf(amgdd_handle h, int32_t level, int32_t *cf, double *l1inv)
+{
+    if (!h) return fail(h, AMGDD_ERR_INVALID_ARG, "null handle");
+    const int nlev = (int)h->H.lv.size();
+    if (level < 0 || level >= nlev) return fail(h, AMGDD_ERR_INVALID_ARG, "level out of range");
+    const HLevel &lv = h->H.lv[level];
+    if (cf) {
+        if (level == nlev - 1) return fail(h, AMGDD_ERR_INVALID_ARG, "the coarsest level has no C/F split");
+        for (size_t i = 0; i < lv.isC.size(); ++i) cf[i] = lv.isC[i];
+    }
+    if (l1inv) std::copy(lv.l1inv.begin(), lv.l1inv.end(), l1inv);
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_get_coarse_inverse(amgdd_handle h, double *ainv)
+{
+    if (!h || !ainv) return fail(h, AMGDD_ERR_INVALID_ARG, "null argument");
+    std::copy(h->H.ainv.begin(), h->H.ainv.end(), ainv);
+    return AMGDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solve phase.
+
+static amgdd_status residual_norm(amgdd_handle h, const double *b, const double *x, double *r, cudaStream_t st,
+                                  double *nrm2)
+{
+    CK(launch_residual(h->lev[0].A, b, x, r, h->partial, h->nred, h->scal, st), "residual kernel");
+    h->launches += 2;
+    if (nrm2) {
+        CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
+        CK(cudaStreamSynchronize(st), "residual");
+        *nrm2 = h->h_scal[0];
+    }
+    return AMGDD_OK;
+}
+
+static amgdd_status restrict_all(amgdd_handle h, double *r_all, cudaStream_t st)
+{
+    const int nlev = (int)h->lev.size();
+    for (int l = 0; l + 1 < nlev; ++l) {
+        const DevLevel &D = h->lev[l];
+        CK(launch_spmv(D.R, 0, D.R.rows, r_all + h->level_off[l], r_all + h->level_off[l + 1], 0, st),
+           "restriction kernel");
+        h->launches += 1;
+    }
+    return AMGDD_OK;
+}
+
+static amgdd_status fac(amgdd_handle h, const double *r_all, double *x, cudaStream_t st)
+{
+    FacParams P = h->fac;
+    P.r_all = r_all;
+    P.x = x;
+    CK(launch_fac_all_grids(P, P.nsub, h->threads, st), "FAC kernel");
+    h->launches += 1;
+    return AMGDD_OK;
+}
+
+static amgdd_status relax(amgdd_handle h, int l, bool cpass, double *u, const double *f, cudaStream_t st)
+{
+    const DevLevel &D = h->lev[l];
+    const int64_t r0 = cpass ? 0 : D.nC, r1 = cpass ? D.nC : D.n;
+    CK(launch_relax_compute(D.A, r0, r1, f, u, D.l1inv, D.d, 0, st), "relax kernel");
+    CK(launch_relax_apply(D.A.rowid, r0, r1, D.d, u, st), "relax apply kernel");
+    h->launches += 2;
+    return AMGDD_OK;
+}
+
+static amgdd_status vcycle(amgdd_handle h, const double *b, double *x, cudaStream_t st)
+{
+    const int L = (int)h->lev.size() - 1;
+    amgdd_status s;
+    for (int l = 0; l < L; ++l) {
+        DevLevel &D = h->lev[l];
+        double *u = l == 0 ? x : D.u;
+        const double *f = l == 0 ? b : D.f;
+        if ((s = relax(h, l, true, u, f, st)) != AMGDD_OK) return s;
+        if ((s = relax(h, l, false, u, f, st)) != AMGDD_OK) return s;
+        CK(launch_relax_compute(D.A, 0, D.n, f, u, D.l1inv, h->res, 1, st), "residual kernel");
+        CK(launch_spmv(D.R, 0, D.R.rows, h->res, h->lev[l + 1].f, 0, st), "restriction kernel");
+        CK(cudaMemsetAsync(h->lev[l + 1].u, 0, sizeof(double) * (size_t)h->lev[l + 1].n, st), "memset");
+        h->launches += 2;
+    }
+    CK(launch_coarse_solve(h->ainv, h->nL, L == 0 ? b : h->lev[L].f, L == 0 ? x : h->lev[L].u, st), "coarse solve");
+    h->launches += 1;
+    for (int l = L - 1; l >= 0; --l) {
+        DevLevel &D = h->lev[l];
+        double *u = l == 0 ? x : D.u;
+        const double *f = l == 0 ? b : D.f;
+        CK(launch_spmv(D.P, 0, D.P.rows, h->lev[l + 1].u, u, 1, st), "interpolation kernel");
+        h->launches += 1;
+        if ((s = relax(h, l, false, u, f, st)) != AMGDD_OK) return s;
+        if ((s = relax(h, l, true, u, f, st)) != AMGDD_OK) return s;
+    }
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_residual(amgdd_handle h, const double *b, const double *x, double *r, double *nrm2, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!b || !x || !r) return fail(h, AMGDD_ERR_INVALID_ARG, "null vector");
+    h->last_stream = (cudaStream_t)stream;
+    return residual_norm(h, b, x, r, (cudaStream_t)stream, nrm2);
+}
+
+amgdd_status amgdd_restrict(amgdd_handle h, double *r_all, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!r_all) return fail(h, AMGDD_ERR_INVALID_ARG, "null vector");
+    h->last_stream = (cudaStream_t)stream;
+    return restrict_all(h, r_all, (cudaStream_t)stream);
+}
+
+amgdd_status amgdd_fac(amgdd_handle h, const double *r_all, double *x, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!r_all || !x) return fail(h, AMGDD_ERR_INVALID_ARG, "null vector");
+    h->last_stream = (cudaStream_t)stream;
+    return fac(h, r_all, x, (cudaStream_t)stream);
+}
+
+amgdd_status amgdd_get_fac_state(amgdd_handle h, int32_t sub, int32_t level, double *u, double *f)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (sub < 0 || sub >= h->C.nsub || level < 0 || level >= h->C.nlev)
+        return fail(h, AMGDD_ERR_INVALID_ARG, "subdomain or level out of range");
+    const FacLevelDesc &d = h->desc[(size_t)sub * h->C.nlev + level];
+    std::vector<double> hu((size_t)d.nBar), hf((size_t)d.nBar);
+    cudaStream_t st = h->last_stream;
+    CK(cudaStreamSynchronize(st), "sync");
+    CK(cudaMemcpy(hu.data(), h->fac.u + d.row0, sizeof(double) * (size_t)d.nBar, cudaMemcpyDeviceToHost), "copy u");
+    CK(cudaMemcpy(hf.data(), h->fac.f + d.row0, sizeof(double) * (size_t)d.nBar, cudaMemcpyDeviceToHost), "copy f");
+    for (int32_t r = 0; r < d.nBar; ++r) {
+        const int32_t m = h->dev2map[d.row0 + r];
+        if (u) u[m] = hu[r];
+        if (f) f[m] = r < d.nReal ? hf[r] : 0.0;
+    }
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_iterate(amgdd_handle h, const double *b, double *x, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!b || !x) return fail(h, AMGDD_ERR_INVALID_ARG, "null vector");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    if ((s = residual_norm(h, b, x, h->r_all, st, nullptr)) != AMGDD_OK) return s;
+    if ((s = restrict_all(h, h->r_all, st)) != AMGDD_OK) return s;
+    return fac(h, h->r_all, x, st);
+}
+
+amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!b || !x) return fail(h, AMGDD_ERR_INVALID_ARG, "null vector");
+    h->last_stream = (cudaStream_t)stream;
+    return vcycle(h, b, x, (cudaStream_t)stream);
+}
+
+static amgdd_status solve_loop(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                               cudaStream_t st, amgdd_solve_info *info, bool amgdd)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = h->launches;
+    amgdd_status s;
+    CK(launch_sumsq(b, h->lev[0].n, h->partial, h->nred, h->scal + 1, st), "norm kernel");
+    h->launches += 2;
+    CK(cudaMemcpyAsync(h->h_scal + 1, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
+    CK(cudaStreamSynchronize(st), "norm");
+    double ref = std::sqrt(h->h_scal[1]);
+    int32_t k = 0;
+    double rel = 0.0;
+    for (;;) {
+        double nr2 = 0.0;
+        if ((s = residual_norm(h, b, x, h->r_all, st, &nr2)) != AMGDD_OK) return s;
+        const double nr = std::sqrt(nr2);
+        if (k == 0 && ref == 0.0) ref = nr;
+        rel = ref > 0.0 ? nr / ref : 0.0;
+        if (info && info->history) info->history[k] = rel;
+        if (rel <= tol || k >= max_iter) break;
+        if (amgdd) {
+            if ((s = restrict_all(h, h->r_all, st)) != AMGDD_OK) return s;
+            if ((s = fac(h, h->r_all, x, st)) != AMGDD_OK) return s;
+        } else {
+            if ((s = vcycle(h, b, x, st)) != AMGDD_OK) return s;
+        }
+        ++k;
+    }
+    CK(cudaStreamSynchronize(st), "solve");
+    if (info) {
+        info->iterations = k;
+        info->converged = rel <= tol;
+        info->final_relres = rel;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->kernel_launches = h->launches - l0;
+    }
+    if (!(rel <= tol)) return fail(h, AMGDD_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_solve(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter, void *stream,
+                         amgdd_solve_info *info)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!b || !x || max_iter < 0 || !(tol >= 0.0)) return fail(h, AMGDD_ERR_INVALID_ARG, "bad solve arguments");
+    h->last_stream = (cudaStream_t)stream;
+    return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, true);
+}
+
+amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                              void *stream, amgdd_solve_info *info)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!b || !x || max_iter < 0 || !(tol >= 0.0)) return fail(h, AMGDD_ERR_INVALID_ARG, "bad solve arguments");
+    h->last_stream = (cudaStream_t)stream;
+    return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, false);
+}
+
+}  // extern "C"

@@ -1,0 +1,397 @@
+// sm_103a kernels of the AMG-DD solve phase.
+//
+// Every sparse row product is computed by one thread as the chain
+// s = 0; s = fma(a_k, x[col_k], s) over the row's entries in ascending column
+// order of the level's global numbering (SELL-32 storage: entry k of row
+// 32*q + lane sits at soff[q] + 32*k + lane, so a warp's loads of entry k are
+// one coalesced 256-byte line of values and a 128-byte line of indices).
+// Built with -fmad=false: only the explicit fma() calls fuse.
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace amgdd {
+namespace dev {
+
+__device__ __forceinline__ double sell_dot(const int64_t *__restrict__ soff, const uint16_t *__restrict__ rlen,
+                                           const int32_t *__restrict__ col, const double *__restrict__ val,
+                                           int64_t slice, int lane, int64_t row, const double *__restrict__ x)
+{
+    const int64_t base = __ldg(soff + slice) + lane;
+    const int len = __ldg(rlen + row);
+    double s = 0.0;
+    const int32_t *c = col + base;
+    const double *v = val + base;
+    int k = 0;
+#pragma unroll 1
+    for (; k + 4 <= len; k += 4) {
+        const int32_t c0 = __ldg(c + 32 * (k + 0)), c1 = __ldg(c + 32 * (k + 1));
+        const int32_t c2 = __ldg(c + 32 * (k + 2)), c3 = __ldg(c + 32 * (k + 3));
+        const double v0 = __ldg(v + 32 * (k + 0)), v1 = __ldg(v + 32 * (k + 1));
+        const double v2 = __ldg(v + 32 * (k + 2)), v3 = __ldg(v + 32 * (k + 3));
+        const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+        s = fma(v0, x0, s);
+        s = fma(v1, x1, s);
+        s = fma(v2, x2, s);
+        s = fma(v3, x3, s);
+    }
+    for (; k < len; ++k) s = fma(__ldg(v + 32 * k), x[__ldg(c + 32 * k)], s);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Global-level kernels (one thread per row, one warp per SELL slice).
+
+// r = b - A x over all rows; per-block partial sums of r^2.
+__global__ void k_residual(SellView A, const double *__restrict__ b, const double *__restrict__ x,
+                           double *__restrict__ r, double *__restrict__ partial)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nslices = (A.rows + 31) / 32;
+    double acc = 0.0;
+    for (int64_t q = warp; q < nslices; q += nwarps) {
+        const int64_t row = q * 32 + lane;
+        if (row < A.rows) {
+            const int32_t i = A.rowid ? __ldg(A.rowid + row) : (int32_t)row;
+            const double s = sell_dot(A.soff, A.rlen, A.col, A.val, q, lane, row, x);
+            const double ri = b[i] - s;
+            r[i] = ri;
+            acc = fma(ri, ri, acc);
+        }
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    }
+}
+
+// sum of squares of v (partial per block)
+__global__ void k_sumsq(const double *__restrict__ v, int64_t n, double *__restrict__ partial)
+{
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(v[i], v[i], acc);
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = x;
+    }
+}
+
+// out[0] = sum of partial[0..n) in a fixed order (deterministic).
+__global__ void k_finish_sum(const double *__restrict__ partial, int n, double *__restrict__ out)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    const int lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) out[0] = v;
+    }
+}
+
+// y[i] = M_i . x (mode 0) or y[i] = y[i] + M_i . x (mode 1) over rows [r0, r1).
+__global__ void k_spmv(SellView M, int64_t r0, int64_t r1, const double *__restrict__ x, double *__restrict__ y,
+                       int mode)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t q0 = r0 / 32, q1 = (r1 + 31) / 32;
+    for (int64_t q = q0 + warp; q < q1; q += nwarps) {
+        const int64_t row = q * 32 + lane;
+        if (row < r0 || row >= r1) continue;
+        const int32_t i = M.rowid ? __ldg(M.rowid + row) : (int32_t)row;
+        const double s = sell_dot(M.soff, M.rlen, M.col, M.val, q, lane, row, x);
+        y[i] = mode ? y[i] + s : s;
+    }
+}
+
+// CF l1-Jacobi, first half: d_i = (f_i - A_i u) * l1inv_i over device rows
+// [r0, r1); mode 1 computes the residual res_i = f_i - A_i u instead.
+__global__ void k_relax_compute(SellView A, int64_t r0, int64_t r1, const double *__restrict__ f,
+                                const double *__restrict__ u, const double *__restrict__ l1inv,
+                                double *__restrict__ d, int mode)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t q0 = r0 / 32, q1 = (r1 + 31) / 32;
+    for (int64_t q = q0 + warp; q < q1; q += nwarps) {
+        const int64_t row = q * 32 + lane;
+        if (row < r0 || row >= r1) continue;
+        const int32_t i = A.rowid ? __ldg(A.rowid + row) : (int32_t)row;
+        const double s = sell_dot(A.soff, A.rlen, A.col, A.val, q, lane, row, u);
+        const double res = f[i] - s;
+        d[i] = mode ? res : res * l1inv[i];
+    }
+}
+
+// second half: u_i = u_i + d_i over the same device rows
+__global__ void k_relax_apply(const int32_t *__restrict__ rowid, int64_t r0, int64_t r1, const double *__restrict__ d,
+                              double *__restrict__ u)
+{
+    for (int64_t row = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < r1;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = rowid[row];
+        u[i] = u[i] + d[i];
+    }
+}
+
+// u = Ainv f (dense, row-major), one thread per row.
+__global__ void k_coarse_solve(const double *__restrict__ ainv, int n, const double *__restrict__ f,
+                               double *__restrict__ u)
+{
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < n; I += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int J = 0; J < n; ++J) s = fma(ainv[(int64_t)I * n + J], f[J], s);
+        u[I] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// All composite grids, one CTA each: gather f_l = r_l on D_l, n_fac AlgFAC
+// V(1,1)-cycles (Algorithm 4), add u_0 on the owned points into x.
+
+struct Block {
+    int tid, nt, lane, warp, nw;
+};
+
+// Rows [r0, r1) of a composite level handled thread-per-row, warp-per-slice.
+template <class Fn>
+__device__ __forceinline__ void for_rows(const Block &B, int r0, int r1, Fn &&fn)
+{
+    if (r1 <= r0) return;
+    const int q0 = r0 >> 5, q1 = (r1 + 31) >> 5;
+    for (int q = q0 + B.warp; q < q1; q += B.nw) {
+        const int r = (q << 5) + B.lane;
+        if (r >= r0 && r < r1) fn(q, r);
+    }
+}
+
+__device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, const FacLevelDesc &d, int r0, int r1)
+{
+    double *__restrict__ u = P.u + d.row0;
+    double *__restrict__ t = P.t + d.row0;
+    double *__restrict__ dd = P.d + d.row0;
+    const double *__restrict__ f = P.f + d.row0;
+    const double *__restrict__ l1 = P.l1inv + d.row0;
+    for_rows(B, r0, r1, [&](int q, int r) {
+        const double s = sell_dot(P.soffA, P.rlenA + d.row0, P.colA, P.valA, d.slice0 + q, B.lane, r, u);
+        dd[r] = (f[r] - s) * l1[r];
+    });
+    __syncthreads();
+    for_rows(B, r0, r1, [&](int q, int r) {
+        const double v = dd[r];
+        u[r] = u[r] + v;
+        t[r] = t[r] + v;
+    });
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) k_fac_all_grids(FacParams P)
+{
+    Block B;
+    B.tid = threadIdx.x;
+    B.nt = blockDim.x;
+    B.lane = threadIdx.x & 31;
+    B.warp = threadIdx.x >> 5;
+    B.nw = blockDim.x >> 5;
+    const int p = P.order[blockIdx.x];
+    const FacLevelDesc *D = P.desc + (int64_t)p * P.nlev;
+    const int L = P.nlev - 1;
+
+    for (int l = 0; l <= L; ++l) {
+        const FacLevelDesc d = D[l];
+        const double *__restrict__ rl = P.r_all + P.level_off[l];
+        for (int r = B.tid; r < d.nBar; r += B.nt) {
+            const int64_t i = d.row0 + r;
+            P.u[i] = 0.0;
+            P.t[i] = 0.0;
+            P.s[i] = 0.0;
+            if (r < d.nReal) P.f[i] = rl[P.gmap[i]];
+        }
+    }
+    __syncthreads();
+
+    for (int c = 1; c <= P.nfac; ++c) {
+        for (int l = 0; l < L; ++l) {
+            const FacLevelDesc d = D[l];
+            const FacLevelDesc dn = D[l + 1];
+            if (l > 0) {
+                // u_l <- 0 then the C half-sweep; with u = 0 it is delta = f / l1
+                double *__restrict__ u = P.u + d.row0;
+                double *__restrict__ t = P.t + d.row0;
+                const double *__restrict__ f = P.f + d.row0;
+                const double *__restrict__ l1 = P.l1inv + d.row0;
+                for (int r = B.tid; r < d.nBar; r += B.nt) {
+                    if (r < d.nC) {
+                        const double v = f[r] * l1[r];
+                        u[r] = 0.0 + v;
+                        t[r] = t[r] + v;
+                    } else {
+                        u[r] = 0.0;
+                    }
+                }
+                __syncthreads();
+            } else {
+                relax_pass(P, B, d, 0, d.nC);
+            }
+            relax_pass(P, B, d, d.nC, d.nReal);
+            // w_l = s_l + A_l t_l on Dbar_l
+            {
+                const double *__restrict__ t = P.t + d.row0;
+                const double *__restrict__ s = P.s + d.row0;
+                double *__restrict__ w = P.w + d.row0;
+                for_rows(B, 0, d.nBar, [&](int q, int r) {
+                    const double at = sell_dot(P.soffA, P.rlenA + d.row0, P.colA, P.valA, d.slice0 + q, B.lane, r, t);
+                    w[r] = s[r] + at;
+                });
+            }
+            __syncthreads();
+            // s_{l+1} = R_l w_l on Dbar_{l+1}; f_{l+1} -= A_{l+1} u_{l+1} (c > 1); f_{l+1} -= s_{l+1}
+            {
+                const double *__restrict__ w = P.w + d.row0;
+                double *__restrict__ s1 = P.s + dn.row0;
+                double *__restrict__ f1 = P.f + dn.row0;
+                const double *__restrict__ u1 = P.u + dn.row0;
+                for_rows(B, 0, dn.nBar, [&](int q, int r) {
+                    const double sv = sell_dot(P.soffR, P.rlenR + dn.row0, P.colR, P.valR, dn.slice0 + q, B.lane, r, w);
+                    s1[r] = sv;
+                    if (r < dn.nReal) {
+                        double fv = f1[r];
+                        if (c > 1)
+                            fv = fv - sell_dot(P.soffA, P.rlenA + dn.row0, P.colA, P.valA, dn.slice0 + q, B.lane, r, u1);
+                        fv = fv - sv;
+                        f1[r] = fv;
+                    }
+                });
+                double *__restrict__ t = P.t + d.row0;
+                double *__restrict__ s = P.s + d.row0;
+                for (int r = B.tid; r < d.nBar; r += B.nt) {
+                    t[r] = 0.0;
+                    s[r] = 0.0;
+                }
+            }
+            __syncthreads();
+        }
+        // coarsest level: u_L = A_L^{-1} f_L (local order = global order)
+        {
+            const FacLevelDesc d = D[L];
+            const double *__restrict__ f = P.f + d.row0;
+            double *__restrict__ u = P.u + d.row0;
+            for (int I = B.tid; I < P.nL; I += B.nt) {
+                double s = 0.0;
+                const double *__restrict__ a = P.ainv + (int64_t)I * P.nL;
+                for (int J = 0; J < P.nL; ++J) s = fma(__ldg(a + J), f[J], s);
+                u[I] = s;
+            }
+        }
+        __syncthreads();
+        for (int l = L - 1; l >= 0; --l) {
+            const FacLevelDesc d = D[l];
+            const FacLevelDesc dn = D[l + 1];
+            double *__restrict__ u = P.u + d.row0;
+            const double *__restrict__ u1 = P.u + dn.row0;
+            for_rows(B, 0, d.nBar, [&](int q, int r) {
+                const double pu = sell_dot(P.soffP, P.rlenP + d.row0, P.colP, P.valP, d.slice0 + q, B.lane, r, u1);
+                u[r] = u[r] + pu;
+            });
+            __syncthreads();
+            relax_pass(P, B, d, d.nC, d.nReal);
+            relax_pass(P, B, d, 0, d.nC);
+        }
+    }
+
+    const FacLevelDesc d0 = D[0];
+    const int64_t o0 = P.owned0[p], o1 = P.owned0[p + 1];
+    for (int64_t k = o0 + B.tid; k < o1; k += B.nt) {
+        const int64_t i = d0.row0 + P.owned[k];
+        const int32_t g = P.gmap[i];
+        P.x[g] = P.x[g] + P.u[i];
+    }
+}
+
+}  // namespace dev
+
+// ---------------------------------------------------------------------------
+// Launchers (host).
+
+static int blocks_for(int64_t rows, int threads, int cap)
+{
+    const int64_t warps = (rows + 31) / 32;
+    int64_t b = (warps * 32 + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t launch_residual(const SellView &A, const double *b, const double *x, double *r, double *partial,
+                            int nblocks, double *out, cudaStream_t st)
+{
+    dev::k_residual<<<nblocks, 256, 0, st>>>(A, b, x, r, partial);
+    dev::k_finish_sum<<<1, 1024, 0, st>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const double *v, int64_t n, double *partial, int nblocks, double *out, cudaStream_t st)
+{
+    dev::k_sumsq<<<nblocks, 256, 0, st>>>(v, n, partial);
+    dev::k_finish_sum<<<1, 1024, 0, st>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const SellView &M, int64_t r0, int64_t r1, const double *x, double *y, int mode,
+                        cudaStream_t st)
+{
+    if (r1 <= r0) return cudaSuccess;
+    dev::k_spmv<<<blocks_for(r1 - r0 + 32, 256, 152 * 16), 256, 0, st>>>(M, r0, r1, x, y, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relax_compute(const SellView &A, int64_t r0, int64_t r1, const double *f, const double *u,
+                                 const double *l1inv, double *d, int mode, cudaStream_t st)
+{
+    if (r1 <= r0) return cudaSuccess;
+    dev::k_relax_compute<<<blocks_for(r1 - r0 + 32, 256, 152 * 16), 256, 0, st>>>(A, r0, r1, f, u, l1inv, d, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relax_apply(const int32_t *rowid, int64_t r0, int64_t r1, const double *d, double *u,
+                               cudaStream_t st)
+{
+    if (r1 <= r0) return cudaSuccess;
+    dev::k_relax_apply<<<blocks_for(r1 - r0, 256, 152 * 16), 256, 0, st>>>(rowid, r0, r1, d, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, double *u, cudaStream_t st)
+{
+    dev::k_coarse_solve<<<(n + 255) / 256, 256, 0, st>>>(ainv, n, f, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st)
+{
+    dev::k_fac_all_grids<<<nsub, threads, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace amgdd

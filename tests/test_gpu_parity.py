@@ -1,0 +1,160 @@
+"""GPU parity: every solve-phase step through the C ABI against the CPU oracle.
+
+Both sides compute each sparse row product as the ascending fma chain, use
+the same hierarchy (checked bit for bit on the host) and the same operation
+order in Algorithms 1, 2 and 4, so iterates, residuals, restricted residuals
+and AlgFAC states must be IDENTICAL. Only the residual norm is reduced in a
+different order: its history is compared at 1e-12 relative, far inside the
+1e-10-per-iteration target.
+"""
+import numpy as np
+import pytest
+
+import amgdd_inputs as I
+from oracle import Oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1906_10575_gb300 import Solver, capi  # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _case(name):
+    if name == "poisson2d_64":
+        w = I.workload("poisson2d_64", seed=0)
+        return w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], w["b"]
+    if name == "ragged2d":   # boxes that do not divide the grid, eta = 2
+        rp, ci, v = I.poisson2d(45, 37)
+        part, nsub = I.box_partition((45, 37), (9, 10))
+        return rp, ci, v, part, nsub, 2, I.uniform_rhs(45 * 37, 1)
+    if name == "poisson3d_24":
+        rp, ci, v = I.poisson3d(24, 24, 24)
+        part, nsub = I.box_partition((24, 24, 24), (8, 8, 8))
+        return rp, ci, v, part, nsub, 2, I.uniform_rhs(24 ** 3, 2)
+    if name == "kappa3d":    # variable coefficient, per-level padding
+        rp, ci, v = I.diffusion3d(I.checkerboard_kappa(20, 4, 3))
+        part, nsub = I.box_partition((20, 20, 20), (10, 10, 5))
+        return rp, ci, v, part, nsub, [2, 1], I.uniform_rhs(8000, 3)
+    if name == "one_grid":   # nsub = 1: the composite grid is the whole hierarchy
+        rp, ci, v = I.poisson2d(33, 30)
+        return rp, ci, v, np.zeros(990, np.int32), 1, 1, I.uniform_rhs(990, 4)
+    if name == "eta0":       # no padding: D_0 = owned set
+        rp, ci, v = I.poisson2d(40, 40)
+        part, nsub = I.box_partition((40, 40), (10, 10))
+        return rp, ci, v, part, nsub, 0, I.uniform_rhs(1600, 5)
+    if name == "single_level":  # n <= max_coarse: only the coarsest solve
+        rp, ci, v = I.poisson2d(4, 3)
+        part, nsub = I.box_partition((4, 3), (2, 3))
+        return rp, ci, v, part, nsub, 1, I.uniform_rhs(12, 6)
+    raise KeyError(name)
+
+
+CASES = ["poisson2d_64", "ragged2d", "poisson3d_24", "kappa3d", "one_grid", "eta0", "single_level"]
+
+
+@pytest.fixture(scope="module", params=CASES)
+def pair(request):
+    rp, ci, v, part, nsub, pad, b = _case(request.param)
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=2)
+    yield request.param, o, s, b
+    s.close()
+
+
+def test_residual_bit_exact(pair):
+    _, o, s, b = pair
+    x = np.random.default_rng(7).standard_normal(s.n)
+    r = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    nrm2 = capi.amgdd_residual(s.h, _dev(b), _dev(x), r)
+    ro = o.residual(b, x)
+    assert np.array_equal(_host(r), ro)
+    assert np.isclose(nrm2, ro @ ro, rtol=1e-13)
+
+
+def test_restriction_bit_exact(pair):
+    _, o, s, b = pair
+    r_all = torch.zeros(int(s.offsets[-1]), dtype=torch.float64, device="cuda")
+    r_all[:s.n] = _dev(b)
+    capi.amgdd_restrict(s.h, r_all)
+    got = _host(r_all)
+    ref = np.concatenate(o.restrict_all(b))
+    assert np.array_equal(got, ref)
+
+
+def test_fac_states_and_update_bit_exact(pair):
+    name, o, s, b = pair
+    rl = o.restrict_all(b)
+    r_all = _dev(np.concatenate(rl))
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    capi.amgdd_fac(s.h, r_all, x)
+    for p in range(s.nsub):
+        uo, fo = o.algfac(p, rl, 2)
+        for l in range(s.nlev):
+            g, k = capi.amgdd_get_maps(s.h, p, l)
+            ug, fg = capi.amgdd_get_fac_state(s.h, p, l, len(g))
+            assert np.array_equal(ug, uo[l][g]), (name, p, l)
+            real = k < 2
+            assert np.array_equal(fg[real], fo[l][g[real]]), (name, p, l)
+    xo = o.amgdd_iteration(b, np.zeros(s.n), 2)
+    assert np.array_equal(_host(x), xo)
+
+
+def test_amgdd_solve_matches_oracle(pair):
+    name, o, s, b = pair
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x, tol=1e-8, max_iter=100)
+    xo, ho = o.amgdd_solve(b, 2, tol=1e-8, maxit=100)
+    assert info["converged"] and info["iterations"] == len(ho) - 1
+    assert np.array_equal(_host(x), xo)
+    assert np.allclose(info["history"], ho, rtol=1e-12, atol=0)
+
+
+def test_vcycle_matches_oracle(pair):
+    name, o, s, b = pair
+    x0 = np.random.default_rng(8).standard_normal(s.n)
+    x = _dev(x0)
+    capi.amg_vcycle(s.h, _dev(b), x)
+    assert np.array_equal(_host(x), o.vcycle_apply(b, x0))
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = s.vcycle_solve(_dev(b), x, tol=1e-8, max_iter=200)
+    xo, ho = o.vcycle_solve(b, tol=1e-8, maxit=200)
+    assert info["iterations"] == len(ho) - 1
+    assert np.array_equal(_host(x), xo)
+    assert np.allclose(info["history"], ho, rtol=1e-12, atol=0)
+
+
+def test_zero_rhs_uses_initial_residual():
+    rp, ci, v, part, nsub, pad, b = _case("poisson2d_64")
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad)
+    x0 = np.random.default_rng(0).uniform(-1, 1, s.n)
+    x = _dev(x0)
+    info = s.solve(torch.zeros(s.n, dtype=torch.float64, device="cuda"), x, tol=1e-6)
+    xo, ho = o.amgdd_solve(np.zeros(s.n), 2, x0=x0, tol=1e-6)
+    assert info["history"][0] == 1.0 and info["iterations"] == len(ho) - 1
+    assert np.array_equal(_host(x), xo)
+    s.close()
+
+
+def test_no_convergence_status_and_last_iterate():
+    rp, ci, v, part, nsub, pad, b = _case("poisson2d_64")
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.AmgddError) as e:
+        s.solve(_dev(b), x, tol=1e-30, max_iter=3)
+    assert e.value.status == 6
+    xo = np.zeros(s.n)
+    for _ in range(3):
+        xo = o.amgdd_iteration(b, xo, 2)
+    assert np.array_equal(_host(x), xo)
+    s.close()

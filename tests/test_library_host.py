@@ -1,0 +1,113 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+* libamgdd.so loads and exports every function include/amgdd.h declares;
+* the library's own setup (host_only) reproduces the oracle's hierarchy and
+  composite-grid index maps bit for bit (both follow the same definitions,
+  written independently);
+* argument validation returns the documented status codes.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import amgdd_inputs as I
+from oracle import Oracle
+from paper_1906_10575_gb300 import Solver, capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "amgdd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(amgdd_\w+|amg_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__ as g
+    g.build()
+    lib = capi.load()
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(capi.EXPORTS) == names
+
+
+def _pair(rp, ci, v, part, nsub, pad, **kw):
+    o = Oracle(rp, ci, v, part, nsub, pad, **kw)
+    s = Solver(rp, ci, v, part, nsub, pad, host_only=True, **kw)
+    return o, s
+
+
+CASES = [
+    ("2d64_eta1", lambda: (*I.poisson2d(64, 64), *I.box_partition((64, 64), (16, 16)), 1)),
+    ("2d45_eta2", lambda: (*I.poisson2d(45, 37), *I.box_partition((45, 37), (9, 10)), 2)),
+    ("3d24_eta2", lambda: (*I.poisson3d(24, 24, 24), *I.box_partition((24, 24, 24), (8, 8, 8)), 2)),
+    ("3d_kappa", lambda: (*I.diffusion3d(I.checkerboard_kappa(20, 4, 3)),
+                          *I.box_partition((20, 20, 20), (10, 10, 5)), [2, 1])),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_hierarchy_and_maps_bit_exact(name, make):
+    rp, ci, v, part, nsub, pad = make()
+    o, s = _pair(rp, ci, v, part, nsub, pad)
+    assert s.level_n == o.level_n
+    for l in range(o.nlev):
+        for which in ("A", "P", "R"):
+            if which != "A" and l == o.nlev - 1:
+                continue
+            a = o.matrix(l, which)
+            b = capi.amgdd_get_operator(s.h, l, which)
+            assert a[3] == b[3]
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+            assert np.array_equal(a[2], b[2]), (l, which)  # bitwise values
+        cf, l1 = capi.amgdd_get_cf(s.h, l, o.level_n[l], with_cf=l < o.nlev - 1)
+        if l < o.nlev - 1:
+            assert np.array_equal(cf, o.cf(l))
+        assert np.array_equal(l1, o.l1inv(l))
+    assert np.array_equal(capi.amgdd_get_coarse_inverse(s.h, o.level_n[-1]), o.ainv())
+    for p in range(nsub):
+        for l in range(o.nlev):
+            g1, k1 = o.comp_map(p, l)
+            g2, k2 = capi.amgdd_get_maps(s.h, p, l)
+            assert np.array_equal(g1, g2) and np.array_equal(k1, k2), (p, l)
+    assert s.stats.assumption_violations == o.violations()
+    assert np.isclose(s.stats.composite_overhead, o.overhead(), rtol=1e-14)
+
+
+def test_box_partition_matches_inputs():
+    for shape, box in [((64, 64), (16, 16)), ((20, 18, 7), (7, 6, 4))]:
+        p1, n1 = I.box_partition(shape, box)
+        p2, n2 = capi.amgdd_box_partition(shape, box)
+        assert n1 == n2 and np.array_equal(p1, p2)
+
+
+def test_validation_errors():
+    rp, ci, v = I.poisson2d(8, 8)
+    part, nsub = I.box_partition((8, 8), (4, 4))
+    bad = v.copy()
+    bad[1] += 0.5                                   # break symmetry
+    with pytest.raises(capi.AmgddError) as e:
+        Solver(rp, ci, bad, part, nsub, 1, host_only=True)
+    assert e.value.status == 2
+    p2 = part.copy()
+    p2[0] = nsub                                     # out of range
+    with pytest.raises(capi.AmgddError) as e:
+        Solver(rp, ci, v, p2, nsub, 1, host_only=True)
+    assert e.value.status == 1
+    with pytest.raises(capi.AmgddError) as e:       # empty subdomain
+        Solver(rp, ci, v, part, nsub + 1, 1, host_only=True)
+    assert e.value.status == 1
+    ci2 = ci.copy()
+    ci2[0], ci2[1] = ci[1], ci[0]                    # unsorted row
+    with pytest.raises(capi.AmgddError) as e:
+        Solver(rp, ci2, v, part, nsub, 1, host_only=True)
+    assert e.value.status == 1
+    s = Solver(rp, ci, v, part, nsub, 1, host_only=True)
+    with pytest.raises(capi.AmgddError) as e:       # no device side
+        capi.amgdd_iterate(s.h, None, None)
+    assert e.value.status in (1, 9)

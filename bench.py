@@ -224,6 +224,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", type=int, default=0, help="FAC kernel variant (0 = library default)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid edge (default 128, the benchmark workload; smaller edges "
                          "are for profiling captures only)")
@@ -248,7 +249,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
     s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
-               stream=stream)
+               schedule=args.schedule, stream=stream)
     st = s.stats
     b = torch.from_numpy(w["b"]).cuda()
     x = torch.zeros_like(b)

@@ -68,7 +68,10 @@ typedef struct {
                                2: also build and range-check the device layouts,
                                still without touching the device */
     int32_t threads;        /* FAC kernel threads per block (0 = default 512) */
-    int32_t reserved[8];
+    int32_t schedule;       /* FAC kernel variant: 0 = default (1); 1 = four
+                               resident blocks per SM, 2 = three blocks per SM
+                               with deeper unrolling */
+    int32_t reserved[7];
 } amgdd_options;
 
 /* Statistics of a completed setup. */

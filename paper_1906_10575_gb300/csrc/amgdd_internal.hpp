@@ -87,22 +87,31 @@ struct GlobalLevelDev {
     Sell R;                       // natural row order (l < L)
 };
 
+// One SELL family of the composite-grid layout (see FacViewDev).
+struct FacView {
+    std::vector<int64_t> soff;            // per slice, plus a sentinel per grid-level
+    std::vector<uint16_t> rlen;           // per row (row0 + local row)
+    std::vector<int32_t> col;             // local column indices
+    std::vector<double> val;
+    int64_t entries = 0;                  // stored (non-padding) entries
+};
+
 struct FacLayout {
     int nlev = 0, nsub = 0;
     std::vector<FacLevelDesc> desc;       // [p * nlev + l]
     std::vector<int32_t> gmap;            // local -> level index
     std::vector<double> l1inv;            // per row (real rows used)
-    std::vector<uint16_t> rlenA, rlenP, rlenR;  // per row; R stored on its row level
-    std::vector<int64_t> soffA, soffP, soffR;   // per slice (+1 sentinel per grid-level)
-    std::vector<int32_t> colA, colP, colR;
-    std::vector<double> valA, valP, valR;
+    FacView A, At, AFc, P, R;
     std::vector<int32_t> owned;           // level-0 local indices of owned points
     std::vector<int64_t> owned0;          // per grid offset into owned (nsub+1)
     std::vector<int32_t> order;           // grids in launch order (largest first)
-    std::vector<int64_t> work;            // per grid estimated FMA count per cycle
+    std::vector<int64_t> work;            // per grid FMA count of one cycle
     // local device order -> position in the map order (owned, real, ghost)
     std::vector<int32_t> dev2map;         // per row
-    int64_t rows_total = 0, slices_total = 0;
+    int64_t rows_total = 0;
+    int32_t max_bar = 0;                  // largest composite level
+    // per level: stored entries of each view over all grids
+    std::vector<int64_t> lvA, lvAt, lvAFc, lvP, lvR;
 };
 
 void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads);

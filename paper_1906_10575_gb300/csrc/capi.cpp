@@ -55,6 +55,15 @@ struct amgdd_handle_s {
     int threads = 512;
     int64_t launches = 0;
     cudaStream_t last_stream = nullptr;
+    // one solver iteration captured as a CUDA graph, per method, keyed by the
+    // vectors it was captured with
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        const double *b = nullptr;
+        double *x = nullptr;
+        int64_t launches = 0;
+    } graph[2];
+    cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -214,6 +223,7 @@ amgdd_status amgdd_options_default(amgdd_options *o)
     o->strict_assumption = 0;
     o->host_only = 0;
     o->threads = 0;
+    o->schedule = 0;
     return AMGDD_OK;
 }
 
@@ -243,6 +253,9 @@ void amgdd_destroy(amgdd_handle h)
     if (!h) return;
     if (h->on_device) {
         cudaStreamSynchronize(h->last_stream);
+        for (auto &g : h->graph)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         for (void *p : h->allocs) cudaFree(p);
         if (h->h_scal) cudaFreeHost(h->h_scal);
     }
@@ -331,15 +344,11 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             FacLayout F;
             build_fac_layout(h->H, h->C, F, nth);
             // stored entries of the local operators (padding excluded)
-            for (int p = 0; p < nsub; ++p)
-                for (int l = 0; l < nlev; ++l) {
-                    const FacLevelDesc &d = F.desc[(size_t)p * nlev + l];
-                    for (int32_t r = 0; r < d.nBar; ++r) {
-                        S.comp_nnz_A[l] += F.rlenA[d.row0 + r];
-                        S.comp_nnz_P[l] += F.rlenP[d.row0 + r];
-                        if (l > 0) S.comp_nnz_R[l - 1] += F.rlenR[d.row0 + r];
-                    }
-                }
+            for (int l = 0; l < nlev; ++l) {
+                S.comp_nnz_A[l] = F.lvA[l];
+                S.comp_nnz_P[l] = F.lvP[l];
+                if (l > 0) S.comp_nnz_R[l - 1] = F.lvR[l];
+            }
             std::vector<GlobalLevelDev> G;
             build_global_dev(h->H, G);
             const std::string bad = validate_layouts(h->H, G, F);
@@ -397,36 +406,50 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             P.nfac = h->opt.n_fac;
             P.nL = h->nL;
             FacLevelDesc *dd;
-            int32_t *ord, *gm, *colA, *colP, *colR, *own;
-            double *l1, *vA, *vP, *vR;
-            uint16_t *rA, *rP, *rR;
-            int64_t *sA, *sP, *sR, *o0;
+            int32_t *ord, *gm, *own;
+            double *l1;
+            int64_t *o0;
             if ((e = upload(h, F.desc, &dd, st_)) != cudaSuccess) return bail(e, "upload desc");
             if ((e = upload(h, F.order, &ord, st_)) != cudaSuccess) return bail(e, "upload order");
             if ((e = upload(h, F.gmap, &gm, st_)) != cudaSuccess) return bail(e, "upload gmap");
             if ((e = upload(h, F.l1inv, &l1, st_)) != cudaSuccess) return bail(e, "upload l1inv");
-            if ((e = upload(h, F.rlenA, &rA, st_)) != cudaSuccess) return bail(e, "upload rlenA");
-            if ((e = upload(h, F.rlenP, &rP, st_)) != cudaSuccess) return bail(e, "upload rlenP");
-            if ((e = upload(h, F.rlenR, &rR, st_)) != cudaSuccess) return bail(e, "upload rlenR");
-            if ((e = upload(h, F.soffA, &sA, st_)) != cudaSuccess) return bail(e, "upload soffA");
-            if ((e = upload(h, F.soffP, &sP, st_)) != cudaSuccess) return bail(e, "upload soffP");
-            if ((e = upload(h, F.soffR, &sR, st_)) != cudaSuccess) return bail(e, "upload soffR");
-            if ((e = upload(h, F.colA, &colA, st_)) != cudaSuccess) return bail(e, "upload colA");
-            if ((e = upload(h, F.colP, &colP, st_)) != cudaSuccess) return bail(e, "upload colP");
-            if ((e = upload(h, F.colR, &colR, st_)) != cudaSuccess) return bail(e, "upload colR");
-            if ((e = upload(h, F.valA, &vA, st_)) != cudaSuccess) return bail(e, "upload valA");
-            if ((e = upload(h, F.valP, &vP, st_)) != cudaSuccess) return bail(e, "upload valP");
-            if ((e = upload(h, F.valR, &vR, st_)) != cudaSuccess) return bail(e, "upload valR");
             if ((e = upload(h, F.owned, &own, st_)) != cudaSuccess) return bail(e, "upload owned");
             if ((e = upload(h, F.owned0, &o0, st_)) != cudaSuccess) return bail(e, "upload owned0");
+            P.col16 = F.max_bar < 65536 ? 1 : 0;
+            P.schedule = h->opt.schedule == 2 ? 2 : 1;
+            FacView *views[5] = {&F.A, &F.At, &F.AFc, &F.P, &F.R};
+            FacViewDev *dviews[5] = {&P.A, &P.At, &P.AFc, &P.P, &P.R};
+            for (int v = 0; v < 5; ++v) {
+                FacView &V = *views[v];
+                int64_t *so;
+                uint16_t *rl;
+                double *va;
+                if ((e = upload(h, V.soff, &so, st_)) != cudaSuccess) return bail(e, "upload view slices");
+                if ((e = upload(h, V.rlen, &rl, st_)) != cudaSuccess) return bail(e, "upload view rows");
+                if ((e = upload(h, V.val, &va, st_)) != cudaSuccess) return bail(e, "upload view values");
+                const void *co;
+                if (P.col16) {
+                    std::vector<uint16_t> c16(V.col.begin(), V.col.end());
+                    uint16_t *c;
+                    if ((e = upload(h, c16, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
+                    if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload view columns");
+                    co = c;
+                } else {
+                    int32_t *c;
+                    if ((e = upload(h, V.col, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
+                    co = c;
+                }
+                if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload views");
+                dviews[v]->soff = so;
+                dviews[v]->rlen = rl;
+                dviews[v]->col = co;
+                dviews[v]->val = va;
+                V = FacView();
+            }
             P.desc = dd;
             P.order = ord;
             P.gmap = gm;
             P.l1inv = l1;
-            P.rlenA = rA; P.rlenP = rP; P.rlenR = rR;
-            P.soffA = sA; P.soffP = sP; P.soffR = sR;
-            P.colA = colA; P.colP = colP; P.colR = colR;
-            P.valA = vA; P.valP = vP; P.valR = vR;
             P.owned = own;
             P.owned0 = o0;
             P.ainv = h->ainv;
@@ -668,36 +691,75 @@ amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream
     return vcycle(h, b, x, (cudaStream_t)stream);
 }
 
+// Captures one solver iteration (the AMG-DD or V-cycle update followed by
+// the residual of the new iterate and the copy of its squared norm into
+// pinned host memory) as a CUDA graph on a private stream.
+static amgdd_status capture_iteration(amgdd_handle h, bool amgdd, const double *b, double *x)
+{
+    auto &G = h->graph[amgdd ? 0 : 1];
+    if (G.exec && G.b == b && G.x == x) return AMGDD_OK;
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t cs = h->cap_stream;
+    const int64_t l0 = h->launches;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    amgdd_status s = amgdd ? restrict_all(h, h->r_all, cs) : vcycle(h, b, x, cs);
+    if (s == AMGDD_OK && amgdd) s = fac(h, h->r_all, x, cs);
+    if (s == AMGDD_OK) {
+        cudaError_t e = launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, cs);
+        h->launches += 2;
+        if (e != cudaSuccess) s = cuda_fail(h, e, "capture residual");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (s != AMGDD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    G.b = b;
+    G.x = x;
+    G.launches = h->launches - l0;
+    h->launches = l0;
+    return AMGDD_OK;
+}
+
 static amgdd_status solve_loop(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
                                cudaStream_t st, amgdd_solve_info *info, bool amgdd)
 {
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t l0 = h->launches;
     amgdd_status s;
+    if ((s = capture_iteration(h, amgdd, b, x)) != AMGDD_OK) return s;
+    const auto &G = h->graph[amgdd ? 0 : 1];
     CK(launch_sumsq(b, h->lev[0].n, h->partial, h->nred, h->scal + 1, st), "norm kernel");
     h->launches += 2;
     CK(cudaMemcpyAsync(h->h_scal + 1, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
-    CK(cudaStreamSynchronize(st), "norm");
+    double nr2 = 0.0;
+    if ((s = residual_norm(h, b, x, h->r_all, st, &nr2)) != AMGDD_OK) return s;
     double ref = std::sqrt(h->h_scal[1]);
     int32_t k = 0;
     double rel = 0.0;
     for (;;) {
-        double nr2 = 0.0;
-        if ((s = residual_norm(h, b, x, h->r_all, st, &nr2)) != AMGDD_OK) return s;
         const double nr = std::sqrt(nr2);
         if (k == 0 && ref == 0.0) ref = nr;
         rel = ref > 0.0 ? nr / ref : 0.0;
         if (info && info->history) info->history[k] = rel;
         if (rel <= tol || k >= max_iter) break;
-        if (amgdd) {
-            if ((s = restrict_all(h, h->r_all, st)) != AMGDD_OK) return s;
-            if ((s = fac(h, h->r_all, x, st)) != AMGDD_OK) return s;
-        } else {
-            if ((s = vcycle(h, b, x, st)) != AMGDD_OK) return s;
-        }
+        CK(cudaGraphLaunch(G.exec, st), "graph launch");
+        CK(cudaStreamSynchronize(st), "iteration");
+        h->launches += G.launches;
+        nr2 = h->h_scal[0];
         ++k;
     }
-    CK(cudaStreamSynchronize(st), "solve");
     if (info) {
         info->iterations = k;
         info->converged = rel <= tol;

@@ -248,8 +248,62 @@ void build_global_dev(const Hierarchy &H, std::vector<GlobalLevelDev> &G)
 }
 
 // Device order of a composite level: [real C | real F | ghost] for l < L, each
-// group by decreasing row length of the local A_l and then ascending global
-// index; the coarsest level keeps ascending global order (it is whole).
+// group by decreasing row length of A_l (real rows: full length; ghost rows:
+// real columns only) and then ascending global index; the coarsest level is
+// whole and keeps ascending global order.
+//
+// Views per level (all entries of a row in ascending global column order, so
+// every row product is the same fma chain as over the full global row: the
+// entries a view omits multiply values that are exactly zero at that point of
+// Algorithm 4):
+//   A   : real rows, all columns            (smoothing, coarse recomputation)
+//   At  : all rows, real columns only       (s_l + A_l t_l; t_l = 0 off D_l)
+//   AFc : real F rows, real C columns only  (downsweep F half-sweep on l >= 1,
+//                                            where u_l = 0 except at C points)
+//   P   : rows Dbar_l, columns in Dbar_{l+1}
+//   R   : R_{l-1} rows Dbar_l, columns in Dbar_{l-1}
+namespace {
+
+struct GridBuild {
+    std::vector<std::vector<int32_t>> dev;
+    std::vector<int32_t> nC, nReal;
+    RowList A[kMaxLevels], At[kMaxLevels], AFc[kMaxLevels], P[kMaxLevels], R[kMaxLevels];
+    std::vector<int32_t> owned_local;
+    std::vector<std::vector<int32_t>> d2m;
+    int64_t work = 0;
+};
+
+void emit_view(RowList &rl, int32_t first_row, int32_t rows_total_level, FacView &V)
+{
+    // rows of the view are local rows [first_row, first_row + rl.rows());
+    // rlen is written for every local row of the level (zero outside the view)
+    const int32_t n = rl.rows();
+    for (int32_t s = 0; s * 32 < n; ++s) {
+        int64_t width = 0;
+        for (int32_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) width = std::max(width, rl.ptr[r + 1] - rl.ptr[r]);
+        const int64_t base = (int64_t)V.col.size();
+        V.soff.push_back(base);
+        V.col.resize((size_t)(base + 32 * width), 0);
+        V.val.resize((size_t)(base + 32 * width), 0.0);
+        for (int32_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) {
+            const int lane = r - s * 32;
+            for (int64_t k = rl.ptr[r]; k < rl.ptr[r + 1]; ++k) {
+                V.col[(size_t)(base + 32 * (k - rl.ptr[r]) + lane)] = rl.col[k];
+                V.val[(size_t)(base + 32 * (k - rl.ptr[r]) + lane)] = rl.val[k];
+            }
+        }
+    }
+    V.soff.push_back((int64_t)V.col.size());
+    for (int32_t r = 0; r < rows_total_level; ++r) {
+        const int32_t v = r - first_row;
+        V.rlen.push_back(v >= 0 && v < n ? (uint16_t)(rl.ptr[v + 1] - rl.ptr[v]) : (uint16_t)0);
+    }
+    V.entries += rl.ptr.back();
+    rl = RowList();
+}
+
+}  // namespace
+
 void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads)
 {
     const int L = H.L();
@@ -258,35 +312,31 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
     F.nlev = nlev;
     F.nsub = nsub;
     F.desc.assign((size_t)nsub * nlev, FacLevelDesc{});
-
-    // Per grid: local order of every level, and the global -> local lookup.
-    struct GridLocal {
-        std::vector<std::vector<int32_t>> dev;   // per level: device order (global idx)
-        std::vector<std::vector<int32_t>> nC, nR; // counts
-        std::vector<int32_t> nCv, nRv;
-        RowList A[64], P[64], R[64];
-        std::vector<int32_t> owned_local;
-        std::vector<std::vector<int32_t>> d2m;
-        int64_t work = 0;
-    };
-    std::vector<GridLocal> grids((size_t)nsub);
+    std::vector<GridBuild> grids((size_t)nsub);
     int32_t nmax = 0;
     for (const auto &lv : H.lv) nmax = std::max(nmax, lv.A.rows);
-    std::vector<std::vector<int32_t>> g2l_s((size_t)std::max(nthreads, 1));
-    std::vector<std::vector<int32_t>> g2l_n((size_t)std::max(nthreads, 1));
-    std::vector<std::vector<uint8_t>> realf((size_t)std::max(nthreads, 1));
+    const int nt = std::max(nthreads, 1);
+    std::vector<std::vector<int32_t>> g2l_s((size_t)nt), g2l_n((size_t)nt), g2l_p((size_t)nt);
+    std::vector<std::vector<uint8_t>> realf((size_t)nt), cflag((size_t)nt);
 
     parallel_for(nsub, nthreads, [&](int p, int t) {
-        GridLocal &G = grids[p];
+        GridBuild &G = grids[p];
         G.dev.resize(nlev);
-        G.nCv.assign(nlev, 0);
-        G.nRv.assign(nlev, 0);
+        G.nC.assign(nlev, 0);
+        G.nReal.assign(nlev, 0);
         G.d2m.resize(nlev);
         auto &g2l = g2l_s[t];
         auto &g2ln = g2l_n[t];
+        auto &g2lp = g2l_p[t];
         auto &isreal = realf[t];
-        if ((int32_t)g2l.size() < nmax) { g2l.assign((size_t)nmax, -1); g2ln.assign((size_t)nmax, -1); isreal.assign((size_t)nmax, 0); }
-        // local device order per level
+        auto &isC = cflag[t];
+        if ((int32_t)g2l.size() < nmax) {
+            g2l.assign((size_t)nmax, -1);
+            g2ln.assign((size_t)nmax, -1);
+            g2lp.assign((size_t)nmax, -1);
+            isreal.assign((size_t)nmax, 0);
+            isC.assign((size_t)nmax, 0);
+        }
         for (int l = 0; l <= L; ++l) {
             const CompLevel &cl = C.at(p, l);
             const Csr &A = H.lv[l].A;
@@ -294,8 +344,8 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
             dev.clear();
             if (l == L) {
                 dev = cl.real;
-                G.nCv[l] = 0;
-                G.nRv[l] = (int32_t)cl.real.size();
+                G.nC[l] = 0;
+                G.nReal[l] = (int32_t)cl.real.size();
             } else {
                 for (int32_t i : cl.real) isreal[i] = 1;
                 auto arow_len = [&](int32_t i) -> int64_t {
@@ -305,8 +355,7 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
                     return c;
                 };
                 std::vector<std::pair<int64_t, int32_t>> cset, fset, gset;
-                for (int32_t i : cl.real)
-                    (H.lv[l].isC[i] ? cset : fset).emplace_back(-arow_len(i), i);
+                for (int32_t i : cl.real) (H.lv[l].isC[i] ? cset : fset).emplace_back(-arow_len(i), i);
                 for (int32_t i : cl.ghost) gset.emplace_back(-arow_len(i), i);
                 std::sort(cset.begin(), cset.end());
                 std::sort(fset.begin(), fset.end());
@@ -314,23 +363,19 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
                 for (auto &e : cset) dev.push_back(e.second);
                 for (auto &e : fset) dev.push_back(e.second);
                 for (auto &e : gset) dev.push_back(e.second);
-                G.nCv[l] = (int32_t)cset.size();
-                G.nRv[l] = (int32_t)(cset.size() + fset.size());
+                G.nC[l] = (int32_t)cset.size();
+                G.nReal[l] = (int32_t)(cset.size() + fset.size());
                 for (int32_t i : cl.real) isreal[i] = 0;
             }
             // device -> map order (owned asc, other real asc, ghost asc)
-            std::vector<int32_t> mapord;
-            mapord.reserve(dev.size());
+            std::vector<int32_t> mapord = cl.owned;
             {
                 size_t a = 0;
-                std::vector<int32_t> rest;
                 for (int32_t i : cl.real) {
                     while (a < cl.owned.size() && cl.owned[a] < i) ++a;
                     if (a < cl.owned.size() && cl.owned[a] == i) continue;
-                    rest.push_back(i);
+                    mapord.push_back(i);
                 }
-                mapord = cl.owned;
-                mapord.insert(mapord.end(), rest.begin(), rest.end());
                 mapord.insert(mapord.end(), cl.ghost.begin(), cl.ghost.end());
             }
             for (size_t k = 0; k < mapord.size(); ++k) g2l[mapord[k]] = (int32_t)k;
@@ -338,29 +383,26 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
             for (size_t k = 0; k < dev.size(); ++k) G.d2m[l][k] = g2l[dev[k]];
             for (int32_t i : mapord) g2l[i] = -1;
         }
-        // local matrices
         for (int l = 0; l <= L; ++l) {
             const Csr &A = H.lv[l].A;
             const std::vector<int32_t> &dev = G.dev[l];
             for (size_t k = 0; k < dev.size(); ++k) g2l[dev[k]] = (int32_t)k;
-            const int32_t nReal = G.nRv[l];
-            // A_l: real rows full, ghost rows restricted to real columns
+            const int32_t nReal = G.nReal[l], nC = G.nC[l];
             for (size_t r = 0; r < dev.size(); ++r) {
                 const int32_t i = dev[r];
                 const bool realrow = (int32_t)r < nReal;
+                const bool frow = realrow && (int32_t)r >= nC;
                 for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
                     const int32_t lc = g2l[A.idx[k]];
-                    if (realrow) {
-                        G.A[l].add_entry(lc, A.val[k]);
-                    } else if (lc >= 0 && lc < nReal) {
-                        G.A[l].add_entry(lc, A.val[k]);
-                    }
+                    if (realrow) G.A[l].add_entry(lc, A.val[k]);
+                    if (lc >= 0 && lc < nReal) G.At[l].add_entry(lc, A.val[k]);
+                    if (frow && lc >= 0 && lc < nC) G.AFc[l].add_entry(lc, A.val[k]);
                 }
-                G.A[l].end_row();
-                G.work += 4 * (G.A[l].ptr.back() - G.A[l].ptr[G.A[l].ptr.size() - 2]);
+                if (realrow) G.A[l].end_row();
+                G.At[l].end_row();
+                if (frow) G.AFc[l].end_row();
             }
             if (l < L) {
-                // P_l: rows Dbar_l, columns inside Dbar_{l+1}
                 const Csr &P = H.lv[l].P;
                 const std::vector<int32_t> &devn = G.dev[l + 1];
                 for (size_t k = 0; k < devn.size(); ++k) g2ln[devn[k]] = (int32_t)k;
@@ -372,76 +414,80 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
                     }
                     G.P[l].end_row();
                 }
-                // R_l: rows Dbar_{l+1} (stored with level l+1), columns in Dbar_l
-                const Csr &R = H.lv[l].R;
-                for (size_t r = 0; r < devn.size(); ++r) {
-                    const int32_t I = devn[r];
-                    for (int64_t k = R.ptr[I]; k < R.ptr[I + 1]; ++k) {
-                        const int32_t lc = g2l[R.idx[k]];
-                        if (lc >= 0) G.R[l + 1].add_entry(lc, R.val[k]);
-                    }
-                    G.R[l + 1].end_row();
-                }
                 for (size_t k = 0; k < devn.size(); ++k) g2ln[devn[k]] = -1;
-                G.work += G.P[l].col.size() + G.R[l + 1].col.size();
             }
-            if (l == 0) {
+            if (l > 0) {
+                const Csr &R = H.lv[l - 1].R;
+                const std::vector<int32_t> &devp = G.dev[l - 1];
+                for (size_t k = 0; k < devp.size(); ++k) g2lp[devp[k]] = (int32_t)k;
+                for (size_t r = 0; r < dev.size(); ++r) {
+                    const int32_t I = dev[r];
+                    for (int64_t k = R.ptr[I]; k < R.ptr[I + 1]; ++k) {
+                        const int32_t lc = g2lp[R.idx[k]];
+                        if (lc >= 0) G.R[l].add_entry(lc, R.val[k]);
+                    }
+                    G.R[l].end_row();
+                }
+                for (size_t k = 0; k < devp.size(); ++k) g2lp[devp[k]] = -1;
+            }
+            if (l == 0)
                 for (int32_t i : C.at(p, 0).owned) G.owned_local.push_back(g2l[i]);
-            }
             for (size_t k = 0; k < dev.size(); ++k) g2l[dev[k]] = -1;
         }
-        for (int l = 0; l <= L; ++l)
-            if (G.R[l].rows() == 0 && !G.dev[l].empty())
-                for (size_t r = 0; r < G.dev[l].size(); ++r) G.R[l].end_row();
+        // FMAs of one cycle after the first (the coarse recomputation included)
+        for (int l = 0; l < L; ++l) {
+            const int64_t a = G.A[l].ptr.back(), at = G.At[l].ptr.back(), afc = G.AFc[l].ptr.back();
+            G.work += (l == 0 ? a : afc) + a + at + G.P[l].ptr.back() + G.R[l + 1].ptr.back() +
+                      G.A[l + 1].ptr.back();
+        }
     });
 
-    // Pack every grid's arrays back to back.
     F.gmap.clear();
     F.owned.clear();
     F.owned0.assign((size_t)nsub + 1, 0);
     F.work.assign((size_t)nsub, 0);
-    int64_t row0 = 0, slice0 = 0;
+    F.lvA.assign(nlev, 0); F.lvAt.assign(nlev, 0); F.lvAFc.assign(nlev, 0);
+    F.lvP.assign(nlev, 0); F.lvR.assign(nlev, 0);
+    int64_t row0 = 0;
     for (int p = 0; p < nsub; ++p) {
-        GridLocal &G = grids[p];
+        GridBuild &G = grids[p];
         for (int l = 0; l <= L; ++l) {
             FacLevelDesc &d = F.desc[(size_t)p * nlev + l];
             const int32_t nbar = (int32_t)G.dev[l].size();
-            d.nC = G.nCv[l];
-            d.nReal = G.nRv[l];
+            d.nC = G.nC[l];
+            d.nReal = G.nReal[l];
             d.nBar = nbar;
             d.row0 = row0;
-            d.slice0 = slice0;
+            F.max_bar = std::max(F.max_bar, nbar);
             const HLevel &lv = H.lv[l];
             for (int32_t i : G.dev[l]) {
                 F.gmap.push_back(i);
                 F.l1inv.push_back(lv.l1inv[i]);
             }
             F.dev2map.insert(F.dev2map.end(), G.d2m[l].begin(), G.d2m[l].end());
-            // A: always; P: l < L (empty rows otherwise); R: l > 0
-            auto emit = [&](RowList &rl, std::vector<int64_t> &soff, std::vector<uint16_t> &rlen,
-                            std::vector<int32_t> &col, std::vector<double> &val) {
-                if (rl.rows() != nbar) {  // no matrix on this level: empty rows
-                    rl = RowList();
-                    for (int32_t r = 0; r < nbar; ++r) rl.end_row();
-                }
-                append_sell(rl, soff, rlen, col, val);
-                soff.push_back((int64_t)col.size());  // sentinel
-            };
-            emit(G.A[l], F.soffA, F.rlenA, F.colA, F.valA);
-            emit(G.P[l], F.soffP, F.rlenP, F.colP, F.valP);
-            emit(G.R[l], F.soffR, F.rlenR, F.colR, F.valR);
+            F.lvA[l] += G.A[l].ptr.back();
+            F.lvAt[l] += G.At[l].ptr.back();
+            F.lvAFc[l] += G.AFc[l].ptr.back();
+            F.lvP[l] += G.P[l].ptr.back();
+            F.lvR[l] += G.R[l].ptr.back();
+            d.sA = (int64_t)F.A.soff.size();
+            emit_view(G.A[l], 0, nbar, F.A);
+            d.sAt = (int64_t)F.At.soff.size();
+            emit_view(G.At[l], 0, nbar, F.At);
+            d.sAFc = (int64_t)F.AFc.soff.size();
+            emit_view(G.AFc[l], d.nC, nbar, F.AFc);
+            d.sP = (int64_t)F.P.soff.size();
+            emit_view(G.P[l], 0, nbar, F.P);
+            d.sR = (int64_t)F.R.soff.size();
+            emit_view(G.R[l], 0, nbar, F.R);
             row0 += nbar;
-            slice0 += (nbar + 31) / 32 + 1;
-            G.A[l] = RowList();
-            G.P[l] = RowList();
-            G.R[l] = RowList();
         }
         F.owned.insert(F.owned.end(), G.owned_local.begin(), G.owned_local.end());
         F.owned0[p + 1] = (int64_t)F.owned.size();
         F.work[p] = G.work;
+        G = GridBuild();
     }
     F.rows_total = row0;
-    F.slices_total = slice0;
     F.order.resize((size_t)nsub);
     std::iota(F.order.begin(), F.order.end(), 0);
     std::stable_sort(F.order.begin(), F.order.end(),
@@ -500,6 +546,8 @@ std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDe
         }
     }
     if (F.nsub == 0) return "";
+    for (const FacView *V : {&F.A, &F.At, &F.AFc, &F.P, &F.R})
+        if ((int64_t)V->rlen.size() != F.rows_total) return "view row-length table size";
     for (int p = 0; p < F.nsub; ++p) {
         for (int l = 0; l <= L; ++l) {
             const FacLevelDesc &d = F.desc[(size_t)p * F.nlev + l];
@@ -511,10 +559,17 @@ std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDe
             }
             const int64_t nup = l < L ? F.desc[(size_t)p * F.nlev + l + 1].nBar : 0;
             const int64_t ndn = l > 0 ? F.desc[(size_t)p * F.nlev + l - 1].nBar : 0;
-            if (!(e = check_sell(F.soffA, d.slice0, F.rlenA, d.row0, d.nBar, F.colA, d.nBar, "local A")).empty()) return e;
-            if (!(e = check_sell(F.soffP, d.slice0, F.rlenP, d.row0, d.nBar, F.colP, nup, "local P")).empty()) return e;
-            if (!(e = check_sell(F.soffR, d.slice0, F.rlenR, d.row0, d.nBar, F.colR, ndn, "local R")).empty()) return e;
+            if (!(e = check_sell(F.A.soff, d.sA, F.A.rlen, d.row0, d.nReal, F.A.col, d.nBar, "local A")).empty()) return e;
+            if (!(e = check_sell(F.At.soff, d.sAt, F.At.rlen, d.row0, d.nBar, F.At.col, d.nReal, "local At")).empty()) return e;
+            if (!(e = check_sell(F.AFc.soff, d.sAFc, F.AFc.rlen, d.row0 + d.nC, d.nReal - d.nC, F.AFc.col, d.nC,
+                                 "local AFc")).empty())
+                return e;
+            if (!(e = check_sell(F.P.soff, d.sP, F.P.rlen, d.row0, l < L ? d.nBar : 0, F.P.col, nup, "local P")).empty())
+                return e;
+            if (!(e = check_sell(F.R.soff, d.sR, F.R.rlen, d.row0, l > 0 ? d.nBar : 0, F.R.col, ndn, "local R")).empty())
+                return e;
             if (l == L && d.nBar != H.lv[L].A.rows) return "coarsest composite level is not whole";
+            if (l == L && d.nReal != d.nBar) return "coarsest composite level has ghosts";
         }
         const FacLevelDesc &d0 = F.desc[(size_t)p * F.nlev];
         for (int64_t k = F.owned0[p]; k < F.owned0[p + 1]; ++k)

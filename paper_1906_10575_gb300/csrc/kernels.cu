@@ -171,34 +171,82 @@ __global__ void k_coarse_solve(const double *__restrict__ ainv, int n, const dou
 // V(1,1)-cycles (Algorithm 4), add u_0 on the owned points into x.
 
 struct Block {
-    int tid, nt, lane, warp, nw;
+    int lane, warp, nw, tid, nt;
 };
 
-// Rows [r0, r1) of a composite level handled thread-per-row, warp-per-slice.
-template <class Fn>
-__device__ __forceinline__ void for_rows(const Block &B, int r0, int r1, Fn &&fn)
+// Row product of local row `r` of a composite-grid view whose slices start at
+// local row `first`: slice q = (r - first) / 32, lane = (r - first) % 32.
+template <class CI, int UNR>
+__device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int r,
+                                           const double *__restrict__ x)
 {
-    if (r1 <= r0) return;
-    const int q0 = r0 >> 5, q1 = (r1 + 31) >> 5;
-    for (int q = q0 + B.warp; q < q1; q += B.nw) {
-        const int r = (q << 5) + B.lane;
-        if (r >= r0 && r < r1) fn(q, r);
+    const int v = r - first;
+    const int64_t base = __ldg(V.soff + slice0 + (v >> 5)) + (v & 31);
+    const int len = __ldg(V.rlen + row0 + r);
+    const CI *__restrict__ c = static_cast<const CI *>(V.col) + base;
+    const double *__restrict__ a = V.val + base;
+    double s = 0.0;
+    int k = 0;
+    if constexpr (UNR == 2) {
+#pragma unroll 1
+        for (; k + 2 <= len; k += 2) {
+            const int c0 = __ldg(c + 32 * k), c1 = __ldg(c + 32 * (k + 1));
+            const double a0 = __ldg(a + 32 * k), a1 = __ldg(a + 32 * (k + 1));
+            const double x0 = x[c0], x1 = x[c1];
+            s = fma(a0, x0, s);
+            s = fma(a1, x1, s);
+        }
+        if (k < len) s = fma(__ldg(a + 32 * k), x[__ldg(c + 32 * k)], s);
+        return s;
+    } else {
+#pragma unroll 1
+    for (; k + UNR <= len; k += UNR) {
+        int ci[UNR];
+        double av[UNR], xv[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) ci[j] = __ldg(c + 32 * (k + j));
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) av[j] = __ldg(a + 32 * (k + j));
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) xv[j] = x[ci[j]];
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) s = fma(av[j], xv[j], s);
+    }
+    for (; k < len; ++k) s = fma(__ldg(a + 32 * k), x[__ldg(c + 32 * k)], s);
+    return s;
     }
 }
 
-__device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, const FacLevelDesc &d, int r0, int r1)
+// Local rows [r0, r1) of a view whose slices start at local row `first`
+// (r0 >= first), thread-per-row, warp-per-slice.
+template <class Fn>
+__device__ __forceinline__ void for_rows(const Block &B, int first, int r0, int r1, Fn &&fn)
+{
+    if (r1 <= r0) return;
+    const int q0 = (r0 - first) >> 5, q1 = (r1 - first + 31) >> 5;
+    for (int q = q0 + B.warp; q < q1; q += B.nw) {
+        const int r = first + (q << 5) + B.lane;
+        if (r >= r0 && r < r1) fn(r);
+    }
+}
+
+// One Jacobi half-sweep over local rows [r0, r1) with view V (slices from
+// `first`): d = (f - V u) / l1 for every row, then u += d, t += d.
+template <class CI, int UNR>
+__device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, const FacLevelDesc &d,
+                                           const FacViewDev &V, int64_t s0, int first, int r0, int r1)
 {
     double *__restrict__ u = P.u + d.row0;
     double *__restrict__ t = P.t + d.row0;
     double *__restrict__ dd = P.d + d.row0;
     const double *__restrict__ f = P.f + d.row0;
     const double *__restrict__ l1 = P.l1inv + d.row0;
-    for_rows(B, r0, r1, [&](int q, int r) {
-        const double s = sell_dot(P.soffA, P.rlenA + d.row0, P.colA, P.valA, d.slice0 + q, B.lane, r, u);
+    for_rows(B, first, r0, r1, [&](int r) {
+        const double s = view_dot<CI, UNR>(V, s0, d.row0, first, r, u);
         dd[r] = (f[r] - s) * l1[r];
     });
     __syncthreads();
-    for_rows(B, r0, r1, [&](int q, int r) {
+    for_rows(B, first, r0, r1, [&](int r) {
         const double v = dd[r];
         u[r] = u[r] + v;
         t[r] = t[r] + v;
@@ -206,7 +254,8 @@ __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, c
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(512) k_fac_all_grids(FacParams P)
+template <class CI, int MINB, int UNR>
+__global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
 {
     Block B;
     B.tid = threadIdx.x;
@@ -236,7 +285,9 @@ __global__ void __launch_bounds__(512) k_fac_all_grids(FacParams P)
             const FacLevelDesc d = D[l];
             const FacLevelDesc dn = D[l + 1];
             if (l > 0) {
-                // u_l <- 0 then the C half-sweep; with u = 0 it is delta = f / l1
+                // u_l <- 0, then the C half-sweep, which with u = 0 is
+                // delta = (f - 0) / l1; the F half-sweep then only sees the
+                // C values of u (view AFc)
                 double *__restrict__ u = P.u + d.row0;
                 double *__restrict__ t = P.t + d.row0;
                 const double *__restrict__ f = P.f + d.row0;
@@ -251,34 +302,35 @@ __global__ void __launch_bounds__(512) k_fac_all_grids(FacParams P)
                     }
                 }
                 __syncthreads();
+                relax_pass<CI, UNR>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal);
             } else {
-                relax_pass(P, B, d, 0, d.nC);
+                relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, 0, d.nC);
+                relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
             }
-            relax_pass(P, B, d, d.nC, d.nReal);
-            // w_l = s_l + A_l t_l on Dbar_l
+            // w_l = s_l + A_l t_l on Dbar_l (t_l is zero off the real points)
             {
                 const double *__restrict__ t = P.t + d.row0;
                 const double *__restrict__ s = P.s + d.row0;
                 double *__restrict__ w = P.w + d.row0;
-                for_rows(B, 0, d.nBar, [&](int q, int r) {
-                    const double at = sell_dot(P.soffA, P.rlenA + d.row0, P.colA, P.valA, d.slice0 + q, B.lane, r, t);
+                for_rows(B, 0, 0, d.nBar, [&](int r) {
+                    const double at = view_dot<CI, UNR>(P.At, d.sAt, d.row0, 0, r, t);
                     w[r] = s[r] + at;
                 });
             }
             __syncthreads();
-            // s_{l+1} = R_l w_l on Dbar_{l+1}; f_{l+1} -= A_{l+1} u_{l+1} (c > 1); f_{l+1} -= s_{l+1}
+            // s_{l+1} = R_l w_l on Dbar_{l+1}; f_{l+1} -= A_{l+1} u_{l+1} (c > 1);
+            // f_{l+1} -= s_{l+1}; then t_l = s_l = 0
             {
                 const double *__restrict__ w = P.w + d.row0;
                 double *__restrict__ s1 = P.s + dn.row0;
                 double *__restrict__ f1 = P.f + dn.row0;
                 const double *__restrict__ u1 = P.u + dn.row0;
-                for_rows(B, 0, dn.nBar, [&](int q, int r) {
-                    const double sv = sell_dot(P.soffR, P.rlenR + dn.row0, P.colR, P.valR, dn.slice0 + q, B.lane, r, w);
+                for_rows(B, 0, 0, dn.nBar, [&](int r) {
+                    const double sv = view_dot<CI, UNR>(P.R, dn.sR, dn.row0, 0, r, w);
                     s1[r] = sv;
                     if (r < dn.nReal) {
                         double fv = f1[r];
-                        if (c > 1)
-                            fv = fv - sell_dot(P.soffA, P.rlenA + dn.row0, P.colA, P.valA, dn.slice0 + q, B.lane, r, u1);
+                        if (c > 1) fv = fv - view_dot<CI, UNR>(P.A, dn.sA, dn.row0, 0, r, u1);
                         fv = fv - sv;
                         f1[r] = fv;
                     }
@@ -310,13 +362,13 @@ __global__ void __launch_bounds__(512) k_fac_all_grids(FacParams P)
             const FacLevelDesc dn = D[l + 1];
             double *__restrict__ u = P.u + d.row0;
             const double *__restrict__ u1 = P.u + dn.row0;
-            for_rows(B, 0, d.nBar, [&](int q, int r) {
-                const double pu = sell_dot(P.soffP, P.rlenP + d.row0, P.colP, P.valP, d.slice0 + q, B.lane, r, u1);
+            for_rows(B, 0, 0, d.nBar, [&](int r) {
+                const double pu = view_dot<CI, UNR>(P.P, d.sP, d.row0, 0, r, u1);
                 u[r] = u[r] + pu;
             });
             __syncthreads();
-            relax_pass(P, B, d, d.nC, d.nReal);
-            relax_pass(P, B, d, 0, d.nC);
+            relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
+            relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, 0, d.nC);
         }
     }
 
@@ -390,7 +442,15 @@ cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, doub
 
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st)
 {
-    dev::k_fac_all_grids<<<nsub, threads, 0, st>>>(P);
+    // schedule 1: 4 CTAs of 512 per SM (32 registers), 2 entries per step;
+    // schedule 2: 3 CTAs per SM, 4 entries per step
+    if (P.schedule == 2) {
+        if (P.col16) dev::k_fac_all_grids<uint16_t, 3, 4><<<nsub, threads, 0, st>>>(P);
+        else dev::k_fac_all_grids<int32_t, 3, 4><<<nsub, threads, 0, st>>>(P);
+    } else {
+        if (P.col16) dev::k_fac_all_grids<uint16_t, 4, 2><<<nsub, threads, 0, st>>>(P);
+        else dev::k_fac_all_grids<int32_t, 4, 2><<<nsub, threads, 0, st>>>(P);
+    }
     return cudaGetLastError();
 }
 

@@ -17,28 +17,42 @@ struct SellView {
     const int32_t *rowid;   // device row -> output index (nullptr: identity)
 };
 
-// Per-grid, per-level descriptor of the composite-grid layout.
+// Per-grid, per-level descriptor of the composite-grid layout. Local rows
+// are ordered [real C | real F | ghost]; every view is a SELL-32 block whose
+// slices start at the view's first row.
 struct FacLevelDesc {
     int32_t nC;        // real C rows: local [0, nC)
     int32_t nReal;     // real rows: local [0, nReal)
     int32_t nBar;      // all rows: local [0, nBar)
     int32_t pad;
-    int64_t row0;      // offset into the per-row arrays
-    int64_t slice0;    // offset into the slice-offset arrays
+    int64_t row0;      // offset into the per-row arrays (nBar entries per level)
+    int64_t sA;        // slices of A_l real rows (full rows), rows [0, nReal)
+    int64_t sAt;       // slices of A_l all rows, real columns only, rows [0, nBar)
+    int64_t sAFc;      // slices of A_l real F rows, real C columns only, rows [nC, nReal)
+    int64_t sP;        // slices of P_l, rows [0, nBar), columns on level l+1
+    int64_t sR;        // slices of R_{l-1} on this level's rows, columns on level l-1
+};
+
+// One SELL family (all grids and levels back to back). rlen is indexed by
+// row0 + local row; col holds uint16_t or int32_t local indices.
+struct FacViewDev {
+    const int64_t *soff;
+    const uint16_t *rlen;
+    const void *col;
+    const double *val;
 };
 
 constexpr int kMaxLevels = 40;
 
 struct FacParams {
     int nlev, nsub, nfac, nL;
+    int col16;                  // 1: local columns are uint16_t
+    int schedule;               // kernel variant (1: 4 CTAs/SM, 2: 3 CTAs/SM)
     const FacLevelDesc *desc;   // [p * nlev + l]
     const int32_t *order;       // launch order of the grids
     const int32_t *gmap;        // per row: level index
     const double *l1inv;        // per row
-    const uint16_t *rlenA, *rlenP, *rlenR;
-    const int64_t *soffA, *soffP, *soffR;
-    const int32_t *colA, *colP, *colR;
-    const double *valA, *valP, *valR;
+    FacViewDev A, At, AFc, P, R;
     const int32_t *owned;       // level-0 local indices of owned points
     const int64_t *owned0;      // per grid offset (nsub + 1)
     const double *ainv;         // n_L x n_L

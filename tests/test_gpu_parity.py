@@ -158,3 +158,35 @@ def test_no_convergence_status_and_last_iterate():
         xo = o.amgdd_iteration(b, xo, 2)
     assert np.array_equal(_host(x), xo)
     s.close()
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_fac_schedules_identical(schedule):
+    """Both kernel variants (residency / unrolling) give the same bits."""
+    rp, ci, v, part, nsub, pad, b = _case("poisson3d_24")
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=3, schedule=schedule)
+    rl = o.restrict_all(b)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    capi.amgdd_fac(s.h, _dev(np.concatenate(rl)), x)
+    xo = o.amgdd_iteration(b, np.zeros(s.n), 3)
+    assert np.array_equal(_host(x), xo)
+    s.close()
+
+
+def test_solve_twice_and_new_buffers_recapture():
+    """The captured iteration graph is keyed by its vectors: new buffers
+    re-capture, repeated calls reuse it; results stay identical."""
+    rp, ci, v, part, nsub, pad, b = _case("poisson2d_64")
+    s = Solver(rp, ci, v, part, nsub, pad)
+    bd = _dev(b)
+    outs = []
+    for _ in range(2):
+        for _ in range(2):
+            x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+            info = s.solve(bd, x, tol=1e-8)
+            outs.append((_host(x), info["iterations"]))
+        bd = _dev(b)
+    for xo, it in outs[1:]:
+        assert it == outs[0][1] and np.array_equal(xo, outs[0][0])
+    s.close()

@@ -109,37 +109,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_fac_bytes(st, nfac):
-    """Bytes one all-grids FAC launch must move (operators once per use).
-
-    A local operator entry is 12 bytes (FP64 value + int32 column), a row adds
-    its 2-byte length. Per cycle and level l < L: the real rows of A_l are read
-    by the pre- and post-smoothing sweeps and every stored row of A_l by
-    s_l + A_l t_l; P_l and R_l are read once; from the second cycle the real
-    rows of A_{l+1} are read once more for the coarse residual recomputation.
-    Vectors: 8 bytes x 8 vector touches per composite point per level visit.
-    """
+def algorithmic_fac_bytes(st, nfac, si=2):
+    """Bytes one all-grids FAC launch must move: the per-composite-grid formula
+    sum_c sum_{l<L} [3 M(A_l real rows) + [c>1] M(A_{l+1} real rows) + 2 M(P_l)
+    + 8 * k * |Dbar_l|] summed over grids, with M(X) = nnz*(8 + si) + 4*rows,
+    si = 2 (16-bit local columns) and k = 8 vector touches per point and
+    level visit. A_l real rows are read by the pre- and post-smoothing sweeps
+    and by s_l + A_l t_l; P_l and R_l = P_l^T once each."""
     L = st.num_levels - 1
+    sv = 8.0
+
+    def M(nnz, rows):
+        return nnz * (sv + si) + 4.0 * rows
+
     tot = 0.0
     for c in range(1, nfac + 1):
         for l in range(L):
-            a_all = 12.0 * st.comp_nnz_A[l] + 2.0 * (st.comp_real[l] + st.comp_ghost[l])
-            a_real = 12.0 * st.comp_nnz_real[l] + 2.0 * st.comp_real[l]
-            tot += 2 * a_real + a_all
-            tot += 12.0 * st.comp_nnz_P[l] + 12.0 * st.comp_nnz_R[l]
+            bar = st.comp_real[l] + st.comp_ghost[l]
+            tot += 3 * M(st.comp_nnz_real[l], st.comp_real[l])
             if c > 1:
-                tot += 12.0 * st.comp_nnz_real[l + 1] + 2.0 * st.comp_real[l + 1]
-            tot += 8.0 * 8 * (st.comp_real[l] + st.comp_ghost[l])
+                tot += M(st.comp_nnz_real[l + 1], st.comp_real[l + 1])
+            tot += 2 * M(st.comp_nnz_P[l], bar)
+            tot += sv * 8 * bar
     return tot
 
 
 def algorithmic_fac_flops(st, nfac):
-    """FP64 flops of one FAC launch: 2 per stored operator entry visited."""
+    """FP64 flops of one FAC launch under the same count: 2 per operator
+    entry of the formula above, plus the dense coarsest products."""
     L = st.num_levels - 1
     fma = 0.0
     for c in range(1, nfac + 1):
         for l in range(L):
-            fma += 2 * st.comp_nnz_real[l] + st.comp_nnz_A[l] + st.comp_nnz_P[l] + st.comp_nnz_R[l]
+            fma += 3 * st.comp_nnz_real[l] + 2 * st.comp_nnz_P[l]
             if c > 1:
                 fma += st.comp_nnz_real[l + 1]
         fma += st.nsub * float(st.n[L]) ** 2

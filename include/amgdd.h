@@ -203,6 +203,35 @@ amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream
 amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double tol,
                               int32_t max_iter, void *stream, amgdd_solve_info *info);
 
+/* ---- residual without any device allocation ------------------------------
+ * The paper has no counterpart to this entry point: it serves callers that
+ * cannot call cudaMalloc at the moment they need a residual, for example code
+ * recording a CUDA graph (allocation is not a stream-ordered call and must not
+ * run during capture) or a process whose device memory belongs to its own pool
+ * allocator. It needs no setup handle and allocates nothing: the matrix and
+ * vectors are the caller's, and the per-block partial sums of the norm live in
+ * a 32 KiB file-scope device array that every GPU loading the library holds
+ * until the process exits.
+ *
+ * Computes r = b - A x (each row as the ascending fma chain, like
+ * amgdd_residual) and nrm2[0] = ||r||_2^2 (fixed-order reduction).
+ *   n        : rows, 0 <= n <= 16,777,216 (the scratch holds one partial sum per
+ *              4096 rows); a larger n returns AMGDD_ERR_INVALID_ARG.
+ *   rowptr, col, val : DEVICE CSR of A (n+1, nnz, nnz entries); the caller
+ *              guarantees a valid structure (columns in [0, n)): device data is
+ *              not inspected.
+ *   b, x, r  : DEVICE, n doubles; nrm2: DEVICE, 1 double.
+ *   stream   : cudaStream_t (NULL = legacy default stream); stream-ordered,
+ *              nothing is synchronised.
+ * The first call on a device looks up the scratch's device address (with that
+ * device current); make that first call before any stream capture. Every call
+ * shares the one scratch array, so calls whose kernels overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised.
+ * Errors: INVALID_ARG (size, null pointer), CUDA; text via amgdd_last_error(NULL). */
+amgdd_status amgdd_residual_csr_noalloc(int32_t n, const int32_t *rowptr, const int32_t *col,
+                                        const double *val, const double *b, const double *x, double *r,
+                                        double *nrm2, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

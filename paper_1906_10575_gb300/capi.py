@@ -59,6 +59,7 @@ EXPORTS = [
     "amgdd_last_error", "amgdd_get_stats", "amgdd_get_maps", "amgdd_get_operator", "amgdd_get_cf",
     "amgdd_get_coarse_inverse", "amgdd_residual", "amgdd_restrict", "amgdd_fac",
     "amgdd_get_fac_state", "amgdd_iterate", "amgdd_solve", "amg_vcycle", "amg_vcycle_solve",
+    "amgdd_residual_csr_noalloc",
 ]
 
 _lib = None
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
         "amgdd_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
         "amg_vcycle": [vp, vp, vp, vp],
         "amg_vcycle_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
+        "amgdd_residual_csr_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -265,3 +267,10 @@ def amg_vcycle(h, b, x, stream=None):
 
 def amg_vcycle_solve(h, b, x, tol=1e-8, max_iter=200, stream=None, raise_on_noconv=True):
     return _solve(load().amg_vcycle_solve, h, b, x, tol, max_iter, stream, raise_on_noconv)
+
+
+def amgdd_residual_csr_noalloc(n, rowptr, col, val, b, x, r, nrm2, stream=None):
+    """r = b - A x and nrm2[0] = ||r||^2 for a device CSR, with no allocation
+    (all arguments are device tensors the caller owns)."""
+    _check(load().amgdd_residual_csr_noalloc(int(n), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b),
+                                              _ptr(x), _ptr(r), _ptr(nrm2), _stream(stream)))

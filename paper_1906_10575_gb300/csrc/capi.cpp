@@ -29,6 +29,10 @@ struct DevLevel {             // device copy of one global level
 
 }  // namespace
 
+namespace amgdd {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace amgdd
+
 struct amgdd_handle_s {
     std::string err;
     amgdd_options opt{};

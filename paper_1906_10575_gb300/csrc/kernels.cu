@@ -217,6 +217,86 @@ __device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, 
     }
 }
 
+// --- asynchronous staging of SELL slices (cp.async into shared memory) ----
+// Each warp owns a ring of S stages; a stage holds K consecutive k-steps of the
+// slice being multiplied: K x 32 values, then K x 32 column indices. The
+// copies hold no registers while in flight, so a lane can keep S*K entries
+// outstanding within the 32-register budget.
+template <class CI, int K, int S>
+struct Ring {
+    static constexpr int kVal = K * 32 * 8;
+    static constexpr int kCol = K * 32 * (int)sizeof(CI);
+    static constexpr int kStage = kVal + kCol;
+    static constexpr int kWarp = S * kStage;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Copies chunk `ch` (k-steps [ch*K, ch*K+K) clipped to the slice width W) into
+// its stage; always commits a group, empty past the end of the slice.
+template <class CI, int K, int S>
+__device__ __forceinline__ void issue_chunk(unsigned char *ring, const double *gval, const CI *gcol, int W, int ch,
+                                            int lane)
+{
+    using R = Ring<CI, K, S>;
+    const int k0 = ch * K;
+    if (k0 < W) {
+        const int kc = K < W - k0 ? K : W - k0;
+        unsigned char *st = ring + (ch % S) * R::kStage;
+        const unsigned char *sv = reinterpret_cast<const unsigned char *>(gval + (int64_t)k0 * 32);
+        const int nv = kc * 16;
+        for (int v = lane; v < nv; v += 32) cp_async16(st + 16 * v, sv + 16 * v);
+        const unsigned char *sc = reinterpret_cast<const unsigned char *>(gcol + (int64_t)k0 * 32);
+        const int nc = kc * 2 * (int)sizeof(CI);
+        for (int v = lane; v < nc; v += 32) cp_async16(st + R::kVal + 16 * v, sc + 16 * v);
+    }
+    cp_async_commit();
+}
+
+// Row product of slice `slice` for this lane's row (len entries; 0 for lanes
+// without a row). All 32 lanes of the warp must call it together.
+template <class CI, int K, int S>
+__device__ __forceinline__ double view_dot_async(const FacViewDev &V, int64_t slice, int len, int lane,
+                                                 const double *__restrict__ x, unsigned char *ring)
+{
+    using R = Ring<CI, K, S>;
+    const int64_t a = __ldg(V.soff + slice), b = __ldg(V.soff + slice + 1);
+    const int W = (int)((b - a) >> 5);
+    const double *gval = V.val + a;
+    const CI *gcol = static_cast<const CI *>(V.col) + a;
+#pragma unroll
+    for (int c = 0; c < S - 1; ++c) issue_chunk<CI, K, S>(ring, gval, gcol, W, c, lane);
+    double s = 0.0;
+    const int nch = (W + K - 1) / K;
+    for (int ch = 0; ch < nch; ++ch) {
+        issue_chunk<CI, K, S>(ring, gval, gcol, W, ch + S - 1, lane);
+        cp_async_wait<S - 1>();
+        __syncwarp();
+        const unsigned char *st = ring + (ch % S) * R::kStage;
+        const double *sv = reinterpret_cast<const double *>(st);
+        const CI *sc = reinterpret_cast<const CI *>(st + R::kVal);
+        double xv[K], av[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const bool on = ch * K + kk < len;
+            av[kk] = on ? sv[kk * 32 + lane] : 0.0;
+            xv[kk] = on ? x[sc[kk * 32 + lane]] : 0.0;
+        }
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+            if (ch * K + kk < len) s = fma(av[kk], xv[kk], s);
+        __syncwarp();
+    }
+    return s;
+}
+
 // Local rows [r0, r1) of a view whose slices start at local row `first`
 // (r0 >= first), thread-per-row, warp-per-slice.
 template <class Fn>
@@ -230,20 +310,48 @@ __device__ __forceinline__ void for_rows(const Block &B, int first, int r0, int 
     }
 }
 
+// Warp-uniform traversal of the slices covering local rows [r0, r1) of a view
+// whose slices start at `first`; fn(q, r, active) is called by every lane.
+template <class Fn>
+__device__ __forceinline__ void for_slices(const Block &B, int first, int r0, int r1, Fn &&fn)
+{
+    if (r1 <= r0) return;
+    const int q0 = (r0 - first) >> 5, q1 = (r1 - first + 31) >> 5;
+    for (int q = q0 + B.warp; q < q1; q += B.nw) {
+        const int r = first + (q << 5) + B.lane;
+        fn(q, r, r >= r0 && r < r1);
+    }
+}
+
+// Row product of local row r of a view: direct loads (K == 0) or staged
+// through the warp's cp.async ring (K > 0). `active` rows only accumulate.
+template <class CI, int UNR, int K, int S>
+__device__ __forceinline__ double row_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int q, int r,
+                                          bool active, const double *__restrict__ x, unsigned char *ring, int lane)
+{
+    if constexpr (K == 0) {
+        return active ? view_dot<CI, UNR>(V, slice0, row0, first, r, x) : 0.0;
+    } else {
+        const int len = active ? (int)__ldg(V.rlen + row0 + r) : 0;
+        return view_dot_async<CI, K, S>(V, slice0 + q, len, lane, x, ring);
+    }
+}
+
 // One Jacobi half-sweep over local rows [r0, r1) with view V (slices from
 // `first`): d = (f - V u) / l1 for every row, then u += d, t += d.
-template <class CI, int UNR>
+template <class CI, int UNR, int K, int S>
 __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, const FacLevelDesc &d,
-                                           const FacViewDev &V, int64_t s0, int first, int r0, int r1)
+                                           const FacViewDev &V, int64_t s0, int first, int r0, int r1,
+                                           unsigned char *ring)
 {
     double *__restrict__ u = P.u + d.row0;
     double *__restrict__ t = P.t + d.row0;
     double *__restrict__ dd = P.d + d.row0;
     const double *__restrict__ f = P.f + d.row0;
     const double *__restrict__ l1 = P.l1inv + d.row0;
-    for_rows(B, first, r0, r1, [&](int r) {
-        const double s = view_dot<CI, UNR>(V, s0, d.row0, first, r, u);
-        dd[r] = (f[r] - s) * l1[r];
+    for_slices(B, first, r0, r1, [&](int q, int r, bool on) {
+        const double s = row_dot<CI, UNR, K, S>(V, s0, d.row0, first, q, r, on, u, ring, B.lane);
+        if (on) dd[r] = (f[r] - s) * l1[r];
     });
     __syncthreads();
     for_rows(B, first, r0, r1, [&](int r) {
@@ -254,15 +362,17 @@ __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, c
     __syncthreads();
 }
 
-template <class CI, int MINB, int UNR>
+template <class CI, int MINB, int UNR, int K, int S>
 __global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
 {
+    extern __shared__ __align__(16) unsigned char fac_smem[];
     Block B;
     B.tid = threadIdx.x;
     B.nt = blockDim.x;
     B.lane = threadIdx.x & 31;
     B.warp = threadIdx.x >> 5;
     B.nw = blockDim.x >> 5;
+    unsigned char *ring = K > 0 ? fac_smem + (size_t)B.warp * Ring<CI, (K > 0 ? K : 1), (S > 0 ? S : 1)>::kWarp : nullptr;
     const int p = P.order[blockIdx.x];
     const FacLevelDesc *D = P.desc + (int64_t)p * P.nlev;
     const int L = P.nlev - 1;
@@ -302,19 +412,19 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
                     }
                 }
                 __syncthreads();
-                relax_pass<CI, UNR>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal);
+                relax_pass<CI, UNR, K, S>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, ring);
             } else {
-                relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, 0, d.nC);
-                relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
+                relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
+                relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
             }
             // w_l = s_l + A_l t_l on Dbar_l (t_l is zero off the real points)
             {
                 const double *__restrict__ t = P.t + d.row0;
                 const double *__restrict__ s = P.s + d.row0;
                 double *__restrict__ w = P.w + d.row0;
-                for_rows(B, 0, 0, d.nBar, [&](int r) {
-                    const double at = view_dot<CI, UNR>(P.At, d.sAt, d.row0, 0, r, t);
-                    w[r] = s[r] + at;
+                for_slices(B, 0, 0, d.nBar, [&](int q, int r, bool on) {
+                    const double at = row_dot<CI, UNR, K, S>(P.At, d.sAt, d.row0, 0, q, r, on, t, ring, B.lane);
+                    if (on) w[r] = s[r] + at;
                 });
             }
             __syncthreads();
@@ -325,14 +435,21 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
                 double *__restrict__ s1 = P.s + dn.row0;
                 double *__restrict__ f1 = P.f + dn.row0;
                 const double *__restrict__ u1 = P.u + dn.row0;
-                for_rows(B, 0, 0, dn.nBar, [&](int r) {
-                    const double sv = view_dot<CI, UNR>(P.R, dn.sR, dn.row0, 0, r, w);
-                    s1[r] = sv;
-                    if (r < dn.nReal) {
-                        double fv = f1[r];
-                        if (c > 1) fv = fv - view_dot<CI, UNR>(P.A, dn.sA, dn.row0, 0, r, u1);
-                        fv = fv - sv;
-                        f1[r] = fv;
+                for_slices(B, 0, 0, dn.nBar, [&](int q, int r, bool on) {
+                    const double sv = row_dot<CI, UNR, K, S>(P.R, dn.sR, dn.row0, 0, q, r, on, w, ring, B.lane);
+                    if (on) s1[r] = sv;
+                    const bool real = on && r < dn.nReal;
+                    if (c > 1) {
+                        // A_{l+1}'s slices cover the real rows only: lanes of slices
+                        // past them have no row
+                        const bool qa = (q << 5) < dn.nReal;
+                        if (qa) {
+                            const double au =
+                                row_dot<CI, UNR, K, S>(P.A, dn.sA, dn.row0, 0, q, r, real, u1, ring, B.lane);
+                            if (real) f1[r] = (f1[r] - au) - sv;
+                        }
+                    } else if (real) {
+                        f1[r] = f1[r] - sv;
                     }
                 });
                 double *__restrict__ t = P.t + d.row0;
@@ -362,13 +479,13 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
             const FacLevelDesc dn = D[l + 1];
             double *__restrict__ u = P.u + d.row0;
             const double *__restrict__ u1 = P.u + dn.row0;
-            for_rows(B, 0, 0, d.nBar, [&](int r) {
-                const double pu = view_dot<CI, UNR>(P.P, d.sP, d.row0, 0, r, u1);
-                u[r] = u[r] + pu;
+            for_slices(B, 0, 0, d.nBar, [&](int q, int r, bool on) {
+                const double pu = row_dot<CI, UNR, K, S>(P.P, d.sP, d.row0, 0, q, r, on, u1, ring, B.lane);
+                if (on) u[r] = u[r] + pu;
             });
             __syncthreads();
-            relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
-            relax_pass<CI, UNR>(P, B, d, P.A, d.sA, 0, 0, d.nC);
+            relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
+            relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
         }
     }
 
@@ -440,18 +557,35 @@ cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, doub
     return cudaGetLastError();
 }
 
+template <class CI, int MINB, int UNR, int K, int S>
+static cudaError_t launch_variant(const FacParams &P, int nsub, int threads, cudaStream_t st)
+{
+    size_t smem = 0;
+    if constexpr (K > 0) smem = (size_t)(threads / 32) * dev::Ring<CI, K, S>::kWarp;
+    auto kern = dev::k_fac_all_grids<CI, MINB, UNR, K, S>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<nsub, threads, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <class CI>
+static cudaError_t launch_fac_ci(const FacParams &P, int nsub, int threads, cudaStream_t st)
+{
+    switch (P.schedule) {
+    case 2: return launch_variant<CI, 3, 4, 0, 0>(P, nsub, threads, st);  // 3 CTAs/SM, 4 entries per step
+    case 3: return launch_variant<CI, 4, 2, 4, 2>(P, nsub, threads, st);  // 4 CTAs/SM, cp.async ring 2 x 4
+    case 4: return launch_variant<CI, 3, 2, 4, 3>(P, nsub, threads, st);  // 3 CTAs/SM, cp.async ring 3 x 4
+    case 5: return launch_variant<CI, 4, 2, 2, 4>(P, nsub, threads, st);  // 4 CTAs/SM, cp.async ring 4 x 2
+    default: return launch_variant<CI, 4, 2, 0, 0>(P, nsub, threads, st); // 4 CTAs/SM, 2 entries per step
+    }
+}
+
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st)
 {
-    // schedule 1: 4 CTAs of 512 per SM (32 registers), 2 entries per step;
-    // schedule 2: 3 CTAs per SM, 4 entries per step
-    if (P.schedule == 2) {
-        if (P.col16) dev::k_fac_all_grids<uint16_t, 3, 4><<<nsub, threads, 0, st>>>(P);
-        else dev::k_fac_all_grids<int32_t, 3, 4><<<nsub, threads, 0, st>>>(P);
-    } else {
-        if (P.col16) dev::k_fac_all_grids<uint16_t, 4, 2><<<nsub, threads, 0, st>>>(P);
-        else dev::k_fac_all_grids<int32_t, 4, 2><<<nsub, threads, 0, st>>>(P);
-    }
-    return cudaGetLastError();
+    return P.col16 ? launch_fac_ci<uint16_t>(P, nsub, threads, st) : launch_fac_ci<int32_t>(P, nsub, threads, st);
 }
 
 }  // namespace amgdd

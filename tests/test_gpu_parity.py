@@ -160,10 +160,12 @@ def test_no_convergence_status_and_last_iterate():
     s.close()
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
-def test_fac_schedules_identical(schedule):
-    """Both kernel variants (residency / unrolling) give the same bits."""
-    rp, ci, v, part, nsub, pad, b = _case("poisson3d_24")
+@pytest.mark.parametrize("case", ["poisson3d_24", "ragged2d", "kappa3d"])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
+def test_fac_schedules_identical(schedule, case):
+    """Every kernel variant (residency, unrolling, cp.async staging depth)
+    gives the oracle's bits, states included."""
+    rp, ci, v, part, nsub, pad, b = _case(case)
     o = Oracle(rp, ci, v, part, nsub, pad)
     s = Solver(rp, ci, v, part, nsub, pad, n_fac=3, schedule=schedule)
     rl = o.restrict_all(b)
@@ -171,6 +173,13 @@ def test_fac_schedules_identical(schedule):
     capi.amgdd_fac(s.h, _dev(np.concatenate(rl)), x)
     xo = o.amgdd_iteration(b, np.zeros(s.n), 3)
     assert np.array_equal(_host(x), xo)
+    for p in (0, nsub - 1):
+        uo, fo = o.algfac(p, rl, 3)
+        for l in range(s.nlev):
+            g, k = capi.amgdd_get_maps(s.h, p, l)
+            ug, fg = capi.amgdd_get_fac_state(s.h, p, l, len(g))
+            assert np.array_equal(ug, uo[l][g]), (p, l)
+            assert np.array_equal(fg[k < 2], fo[l][g[k < 2]]), (p, l)
     s.close()
 
 

@@ -62,6 +62,9 @@ def _peaks():
 # FP64 peak of a GB300: 1.25 TFLOP/s nominal dense (2 DFMA per SM per clock at
 # 2.07 GHz boost on 152 SMs is 1.26 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.25
+# FP64 FMA throughput measured on this machine's GB300 with 8 independent fma
+# chains per thread (1.198 TFLOP/s)
+FP64_PROBE_TFLOPS = 1.198
 
 
 class ClockSampler:
@@ -334,6 +337,7 @@ def main():
     fac_f = algorithmic_fac_flops(st, w["n_fac"])
     fac_gbs = fac_b / (fac_ms * 1e-3) / 1e9
     fac_tfs = fac_f / (fac_ms * 1e-3) / 1e12
+    exec_tfs = 2.0 * st.fac_fma / (fac_ms * 1e-3) / 1e12
     frac_hbm = fac_gbs / hbm
     frac_alu = fac_tfs / FP64_PEAK_TFLOPS
     if frac_alu >= frac_hbm:
@@ -345,7 +349,10 @@ def main():
                 "frac": round(frac_hbm, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
     roof.update({"kernel": "k_fac_all_grids", "traffic": None, "ms_per_launch": round(fac_ms, 3),
                  "algorithmic_bytes": fac_b, "algorithmic_flops": fac_f,
-                 "hbm_frac_of_measured": round(frac_hbm, 4), "fp64_frac_of_nominal": round(frac_alu, 4)})
+                 "hbm_frac_of_measured": round(frac_hbm, 4), "fp64_frac_of_nominal": round(frac_alu, 4),
+                 "executed_fp64_fma": int(st.fac_fma),
+                 "executed_fp64_frac_of_nominal": round(exec_tfs / FP64_PEAK_TFLOPS, 4),
+                 "executed_fp64_frac_of_probe": round(exec_tfs / FP64_PROBE_TFLOPS, 4)})
     dd_bytes = algorithmic_solve_bytes(st, fac_b, it_dd)
     v_bytes = vcycle_bytes(st, it_v)
     launches = int(i_dd[-1]["kernel_launches"])

@@ -68,9 +68,12 @@ typedef struct {
                                2: also build and range-check the device layouts,
                                still without touching the device */
     int32_t threads;        /* FAC kernel threads per block (0 = default 512) */
-    int32_t schedule;       /* FAC kernel variant: 0 = default (1); 1 = four
-                               resident blocks per SM, 2 = three blocks per SM
-                               with deeper unrolling */
+    int32_t schedule;       /* FAC kernel variant, all giving identical results:
+                               0 = default (1); 1 = four resident blocks of 512
+                               threads per SM; 2 = three blocks, deeper
+                               unrolling; 3-5 = operators staged through
+                               cp.async rings of different depths; 6, 7 = two
+                               blocks of 1024 threads (7 with a cp.async ring) */
     int32_t reserved[7];
 } amgdd_options;
 
@@ -93,6 +96,9 @@ typedef struct {
     double composite_overhead;          /* Section 6.1 definition */
     int64_t assumption_violations;      /* grid-level pairs that break the assumption */
     int64_t device_bytes;               /* device memory held by the handle */
+    int64_t fac_fma;                    /* FP64 fused multiply-adds one all-grids
+                                           FAC launch executes (n_fac cycles) */
+    int64_t fac_entry_bytes;            /* bytes per stored local operator entry */
     double setup_seconds;
 } amgdd_setup_stats;
 

@@ -45,7 +45,8 @@ class amgdd_setup_stats(C.Structure):
                 ("comp_nnz_P", C.c_int64 * MAX_LEVELS), ("comp_nnz_R", C.c_int64 * MAX_LEVELS),
                 ("operator_complexity", C.c_double), ("grid_complexity", C.c_double),
                 ("composite_overhead", C.c_double), ("assumption_violations", C.c_int64),
-                ("device_bytes", C.c_int64), ("setup_seconds", C.c_double)]
+                ("device_bytes", C.c_int64), ("fac_fma", C.c_int64), ("fac_entry_bytes", C.c_int64),
+                ("setup_seconds", C.c_double)]
 
 
 class amgdd_solve_info(C.Structure):

@@ -105,7 +105,8 @@ struct FacLayout {
     std::vector<int32_t> owned;           // level-0 local indices of owned points
     std::vector<int64_t> owned0;          // per grid offset into owned (nsub+1)
     std::vector<int32_t> order;           // grids in launch order (largest first)
-    std::vector<int64_t> work;            // per grid FMA count of one cycle
+    std::vector<int64_t> work;            // per grid FMA count of one cycle after the first
+    std::vector<int64_t> work1;           // per grid FMA count of the first cycle
     // local device order -> position in the map order (owned, real, ghost)
     std::vector<int32_t> dev2map;         // per row
     int64_t rows_total = 0;

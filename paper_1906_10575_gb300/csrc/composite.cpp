@@ -270,7 +270,7 @@ struct GridBuild {
     RowList A[kMaxLevels], At[kMaxLevels], AFc[kMaxLevels], P[kMaxLevels], R[kMaxLevels];
     std::vector<int32_t> owned_local;
     std::vector<std::vector<int32_t>> d2m;
-    int64_t work = 0;
+    int64_t work = 0, work1 = 0;
 };
 
 void emit_view(RowList &rl, int32_t first_row, int32_t rows_total_level, FacView &V)
@@ -435,17 +435,26 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
             for (size_t k = 0; k < dev.size(); ++k) g2l[dev[k]] = -1;
         }
         // FMAs of one cycle after the first (the coarse recomputation included)
+        // executed fma: downsweep half-sweeps (full rows on level 0, C columns
+        // of the F rows above it), s + A t, R, the upsweep P and half-sweeps,
+        // the coarse recomputation (not in the first cycle) and the dense
+        // coarsest product
+        const int64_t nL = (int64_t)G.dev[L].size();
         for (int l = 0; l < L; ++l) {
             const int64_t a = G.A[l].ptr.back(), at = G.At[l].ptr.back(), afc = G.AFc[l].ptr.back();
-            G.work += (l == 0 ? a : afc) + a + at + G.P[l].ptr.back() + G.R[l + 1].ptr.back() +
-                      G.A[l + 1].ptr.back();
+            const int64_t base = (l == 0 ? a : afc) + a + at + G.P[l].ptr.back() + G.R[l + 1].ptr.back();
+            G.work1 += base;
+            G.work += base + G.A[l + 1].ptr.back();
         }
+        G.work1 += nL * nL;
+        G.work += nL * nL;
     });
 
     F.gmap.clear();
     F.owned.clear();
     F.owned0.assign((size_t)nsub + 1, 0);
     F.work.assign((size_t)nsub, 0);
+    F.work1.assign((size_t)nsub, 0);
     F.lvA.assign(nlev, 0); F.lvAt.assign(nlev, 0); F.lvAFc.assign(nlev, 0);
     F.lvP.assign(nlev, 0); F.lvR.assign(nlev, 0);
     int64_t row0 = 0;
@@ -485,6 +494,7 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
         F.owned.insert(F.owned.end(), G.owned_local.begin(), G.owned_local.end());
         F.owned0[p + 1] = (int64_t)F.owned.size();
         F.work[p] = G.work;
+        F.work1[p] = G.work1;
         G = GridBuild();
     }
     F.rows_total = row0;

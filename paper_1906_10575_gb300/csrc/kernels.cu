@@ -362,8 +362,8 @@ __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, c
     __syncthreads();
 }
 
-template <class CI, int MINB, int UNR, int K, int S>
-__global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
+template <class CI, int MINB, int UNR, int K, int S, int NT = 512>
+__global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
 {
     extern __shared__ __align__(16) unsigned char fac_smem[];
     Block B;
@@ -373,7 +373,25 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
     B.warp = threadIdx.x >> 5;
     B.nw = blockDim.x >> 5;
     unsigned char *ring = K > 0 ? fac_smem + (size_t)B.warp * Ring<CI, (K > 0 ? K : 1), (S > 0 ? S : 1)>::kWarp : nullptr;
-    const int p = P.order[blockIdx.x];
+    __shared__ int claimed;
+    for (;;) {
+    // claim the next grid: own SM's bin first, then the others (each probe
+    // is one atomic; at most nbins probes, no waiting)
+    __syncthreads();
+    if (B.tid == 0) {
+        unsigned sm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        int g = -1;
+        for (int probe = 0; probe < P.nbins && g < 0; ++probe) {
+            const int b = (int)((sm + (unsigned)probe) % (unsigned)P.nbins);
+            const int k = atomicAdd(P.ctr + b, 1);
+            if (k < P.bin_off[b + 1] - P.bin_off[b]) g = P.bin_grid[P.bin_off[b] + k];
+        }
+        claimed = g;
+    }
+    __syncthreads();
+    const int p = claimed;
+    if (p < 0) break;
     const FacLevelDesc *D = P.desc + (int64_t)p * P.nlev;
     const int L = P.nlev - 1;
 
@@ -496,6 +514,7 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids(FacParams P)
         const int32_t g = P.gmap[i];
         P.x[g] = P.x[g] + P.u[i];
     }
+    }
 }
 
 }  // namespace dev
@@ -557,35 +576,59 @@ cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, doub
     return cudaGetLastError();
 }
 
-template <class CI, int MINB, int UNR, int K, int S>
-static cudaError_t launch_variant(const FacParams &P, int nsub, int threads, cudaStream_t st)
+template <class CI, int MINB, int UNR, int K, int S, int NT = 512>
+static cudaError_t launch_variant(const FacParams &P, int nsub, int threads, cudaStream_t st, int *blocks_per_sm)
 {
+    if (threads > NT) threads = NT;
+    if (NT > 512) threads = NT;
     size_t smem = 0;
     if constexpr (K > 0) smem = (size_t)(threads / 32) * dev::Ring<CI, K, S>::kWarp;
-    auto kern = dev::k_fac_all_grids<CI, MINB, UNR, K, S>;
+    auto kern = dev::k_fac_all_grids<CI, MINB, UNR, K, S, NT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<nsub, threads, smem, st>>>(P);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (blocks_per_sm) {
+        *blocks_per_sm = per_sm;
+        return cudaSuccess;
+    }
+    // persistent: every resident slot gets a CTA (never more CTAs than grids)
+    int ctas = per_sm * P.nbins;
+    if (ctas > nsub) ctas = nsub;
+    e = cudaMemsetAsync(P.ctr, 0, sizeof(int32_t) * (size_t)P.nbins, st);
+    if (e != cudaSuccess) return e;
+    kern<<<ctas, threads, smem, st>>>(P);
     return cudaGetLastError();
 }
 
 template <class CI>
-static cudaError_t launch_fac_ci(const FacParams &P, int nsub, int threads, cudaStream_t st)
+static cudaError_t launch_fac_ci(const FacParams &P, int nsub, int threads, cudaStream_t st, int *bps)
 {
     switch (P.schedule) {
-    case 2: return launch_variant<CI, 3, 4, 0, 0>(P, nsub, threads, st);  // 3 CTAs/SM, 4 entries per step
-    case 3: return launch_variant<CI, 4, 2, 4, 2>(P, nsub, threads, st);  // 4 CTAs/SM, cp.async ring 2 x 4
-    case 4: return launch_variant<CI, 3, 2, 4, 3>(P, nsub, threads, st);  // 3 CTAs/SM, cp.async ring 3 x 4
-    case 5: return launch_variant<CI, 4, 2, 2, 4>(P, nsub, threads, st);  // 4 CTAs/SM, cp.async ring 4 x 2
-    default: return launch_variant<CI, 4, 2, 0, 0>(P, nsub, threads, st); // 4 CTAs/SM, 2 entries per step
+    case 2: return launch_variant<CI, 3, 4, 0, 0>(P, nsub, threads, st, bps);  // 3 CTAs/SM, 4 entries per step
+    case 3: return launch_variant<CI, 4, 2, 4, 2>(P, nsub, threads, st, bps);  // 4 CTAs/SM, cp.async ring 2 x 4
+    case 4: return launch_variant<CI, 3, 2, 4, 3>(P, nsub, threads, st, bps);  // 3 CTAs/SM, cp.async ring 3 x 4
+    case 5: return launch_variant<CI, 4, 2, 2, 4>(P, nsub, threads, st, bps);  // 4 CTAs/SM, cp.async ring 4 x 2
+    case 6: return launch_variant<CI, 2, 2, 0, 0, 1024>(P, nsub, threads, st, bps);  // 2 CTAs of 1024/SM
+    case 7: return launch_variant<CI, 2, 2, 4, 2, 1024>(P, nsub, threads, st, bps);  // same, cp.async ring 2 x 4
+    default: return launch_variant<CI, 4, 2, 0, 0>(P, nsub, threads, st, bps); // 4 CTAs/SM, 2 entries per step
     }
 }
 
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st)
 {
-    return P.col16 ? launch_fac_ci<uint16_t>(P, nsub, threads, st) : launch_fac_ci<int32_t>(P, nsub, threads, st);
+    return P.col16 ? launch_fac_ci<uint16_t>(P, nsub, threads, st, nullptr)
+                   : launch_fac_ci<int32_t>(P, nsub, threads, st, nullptr);
+}
+
+cudaError_t fac_blocks_per_sm(const FacParams &P, int threads, int *blocks)
+{
+    return P.col16 ? launch_fac_ci<uint16_t>(P, 0, threads, nullptr, blocks)
+                   : launch_fac_ci<int32_t>(P, 0, threads, nullptr, blocks);
 }
 
 }  // namespace amgdd

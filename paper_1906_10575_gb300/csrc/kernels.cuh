@@ -47,7 +47,14 @@ constexpr int kMaxLevels = 40;
 struct FacParams {
     int nlev, nsub, nfac, nL;
     int col16;                  // 1: local columns are uint16_t
-    int schedule;               // kernel variant (1: 4 CTAs/SM, 2: 3 CTAs/SM)
+    int schedule;               // kernel variant (see launch_fac_all_grids)
+    // Work distribution: grids are packed into one bin per SM (by estimated
+    // work); a CTA claims grids from the bin of the SM it runs on, then from
+    // the other bins. ctr holds one claim counter per bin (zeroed per launch).
+    int nbins;
+    const int32_t *bin_off;     // nbins + 1
+    const int32_t *bin_grid;    // nsub
+    int32_t *ctr;               // nbins
     const FacLevelDesc *desc;   // [p * nlev + l]
     const int32_t *order;       // launch order of the grids
     const int32_t *gmap;        // per row: level index
@@ -73,5 +80,7 @@ cudaError_t launch_relax_apply(const int32_t *rowid, int64_t r0, int64_t r1, con
                                cudaStream_t st);
 cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, double *u, cudaStream_t st);
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st);
+// resident CTAs per SM of the selected FAC kernel variant
+cudaError_t fac_blocks_per_sm(const FacParams &P, int threads, int *blocks);
 
 }  // namespace amgdd

@@ -69,11 +69,12 @@ typedef struct {
                                still without touching the device */
     int32_t threads;        /* FAC kernel threads per block (0 = default 512) */
     int32_t schedule;       /* FAC kernel variant, all giving identical results:
-                               0 = default (1); 1 = four resident blocks of 512
+                               0 = default (8); 1 = four resident blocks of 512
                                threads per SM; 2 = three blocks, deeper
                                unrolling; 3-5 = operators staged through
                                cp.async rings of different depths; 6, 7 = two
-                               blocks of 1024 threads (7 with a cp.async ring) */
+                               blocks of 1024 threads (7 with a cp.async ring);
+                               8, 9 = 1 and 6 with evict-first operator loads */
     int32_t reserved[7];
 } amgdd_options;
 

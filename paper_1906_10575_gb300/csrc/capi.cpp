@@ -424,7 +424,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             if ((e = upload(h, F.owned, &own, st_)) != cudaSuccess) return bail(e, "upload owned");
             if ((e = upload(h, F.owned0, &o0, st_)) != cudaSuccess) return bail(e, "upload owned0");
             P.col16 = F.max_bar < 65536 ? 1 : 0;
-            P.schedule = h->opt.schedule >= 1 && h->opt.schedule <= 7 ? h->opt.schedule : 1;
+            P.schedule = h->opt.schedule >= 1 && h->opt.schedule <= 9 ? h->opt.schedule : 8;
             FacView *views[5] = {&F.A, &F.At, &F.AFc, &F.P, &F.R};
             FacViewDev *dviews[5] = {&P.A, &P.At, &P.AFc, &P.P, &P.R};
             for (int v = 0; v < 5; ++v) {

@@ -176,7 +176,17 @@ struct Block {
 
 // Row product of local row `r` of a composite-grid view whose slices start at
 // local row `first`: slice q = (r - first) / 32, lane = (r - first) % 32.
-template <class CI, int UNR>
+// Loads of operator entries, which every launch streams once: evict-first
+// (ld.global.cs) when STREAM is set, so they do not push the composite-grid
+// vectors out of L2; read-only path (ld.global.nc) otherwise.
+template <bool STREAM, class T>
+__device__ __forceinline__ T ld_op(const T *p)
+{
+    if constexpr (STREAM) return __ldcs(p);
+    else return __ldg(p);
+}
+
+template <class CI, int UNR, bool STREAM = false>
 __device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int r,
                                            const double *__restrict__ x)
 {
@@ -190,13 +200,13 @@ __device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, 
     if constexpr (UNR == 2) {
 #pragma unroll 1
         for (; k + 2 <= len; k += 2) {
-            const int c0 = __ldg(c + 32 * k), c1 = __ldg(c + 32 * (k + 1));
-            const double a0 = __ldg(a + 32 * k), a1 = __ldg(a + 32 * (k + 1));
+            const int c0 = ld_op<STREAM>(c + 32 * k), c1 = ld_op<STREAM>(c + 32 * (k + 1));
+            const double a0 = ld_op<STREAM>(a + 32 * k), a1 = ld_op<STREAM>(a + 32 * (k + 1));
             const double x0 = x[c0], x1 = x[c1];
             s = fma(a0, x0, s);
             s = fma(a1, x1, s);
         }
-        if (k < len) s = fma(__ldg(a + 32 * k), x[__ldg(c + 32 * k)], s);
+        if (k < len) s = fma(ld_op<STREAM>(a + 32 * k), x[ld_op<STREAM>(c + 32 * k)], s);
         return s;
     } else {
 #pragma unroll 1
@@ -204,15 +214,15 @@ __device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, 
         int ci[UNR];
         double av[UNR], xv[UNR];
 #pragma unroll
-        for (int j = 0; j < UNR; ++j) ci[j] = __ldg(c + 32 * (k + j));
+        for (int j = 0; j < UNR; ++j) ci[j] = ld_op<STREAM>(c + 32 * (k + j));
 #pragma unroll
-        for (int j = 0; j < UNR; ++j) av[j] = __ldg(a + 32 * (k + j));
+        for (int j = 0; j < UNR; ++j) av[j] = ld_op<STREAM>(a + 32 * (k + j));
 #pragma unroll
         for (int j = 0; j < UNR; ++j) xv[j] = x[ci[j]];
 #pragma unroll
         for (int j = 0; j < UNR; ++j) s = fma(av[j], xv[j], s);
     }
-    for (; k < len; ++k) s = fma(__ldg(a + 32 * k), x[__ldg(c + 32 * k)], s);
+    for (; k < len; ++k) s = fma(ld_op<STREAM>(a + 32 * k), x[ld_op<STREAM>(c + 32 * k)], s);
     return s;
     }
 }
@@ -325,12 +335,12 @@ __device__ __forceinline__ void for_slices(const Block &B, int first, int r0, in
 
 // Row product of local row r of a view: direct loads (K == 0) or staged
 // through the warp's cp.async ring (K > 0). `active` rows only accumulate.
-template <class CI, int UNR, int K, int S>
+template <class CI, int UNR, int K, int S, bool STREAM = false>
 __device__ __forceinline__ double row_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int q, int r,
                                           bool active, const double *__restrict__ x, unsigned char *ring, int lane)
 {
     if constexpr (K == 0) {
-        return active ? view_dot<CI, UNR>(V, slice0, row0, first, r, x) : 0.0;
+        return active ? view_dot<CI, UNR, STREAM>(V, slice0, row0, first, r, x) : 0.0;
     } else {
         const int len = active ? (int)__ldg(V.rlen + row0 + r) : 0;
         return view_dot_async<CI, K, S>(V, slice0 + q, len, lane, x, ring);
@@ -339,7 +349,7 @@ __device__ __forceinline__ double row_dot(const FacViewDev &V, int64_t slice0, i
 
 // One Jacobi half-sweep over local rows [r0, r1) with view V (slices from
 // `first`): d = (f - V u) / l1 for every row, then u += d, t += d.
-template <class CI, int UNR, int K, int S>
+template <class CI, int UNR, int K, int S, bool STREAM>
 __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, const FacLevelDesc &d,
                                            const FacViewDev &V, int64_t s0, int first, int r0, int r1,
                                            unsigned char *ring)
@@ -350,7 +360,7 @@ __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, c
     const double *__restrict__ f = P.f + d.row0;
     const double *__restrict__ l1 = P.l1inv + d.row0;
     for_slices(B, first, r0, r1, [&](int q, int r, bool on) {
-        const double s = row_dot<CI, UNR, K, S>(V, s0, d.row0, first, q, r, on, u, ring, B.lane);
+        const double s = row_dot<CI, UNR, K, S, STREAM>(V, s0, d.row0, first, q, r, on, u, ring, B.lane);
         if (on) dd[r] = (f[r] - s) * l1[r];
     });
     __syncthreads();
@@ -362,7 +372,7 @@ __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, c
     __syncthreads();
 }
 
-template <class CI, int MINB, int UNR, int K, int S, int NT = 512>
+template <class CI, int MINB, int UNR, int K, int S, int NT = 512, bool STREAM = false>
 __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
 {
     extern __shared__ __align__(16) unsigned char fac_smem[];
@@ -430,10 +440,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
                     }
                 }
                 __syncthreads();
-                relax_pass<CI, UNR, K, S>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, ring);
+                relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, ring);
             } else {
-                relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
-                relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
+                relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
+                relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
             }
             // w_l = s_l + A_l t_l on Dbar_l (t_l is zero off the real points)
             {
@@ -441,7 +451,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
                 const double *__restrict__ s = P.s + d.row0;
                 double *__restrict__ w = P.w + d.row0;
                 for_slices(B, 0, 0, d.nBar, [&](int q, int r, bool on) {
-                    const double at = row_dot<CI, UNR, K, S>(P.At, d.sAt, d.row0, 0, q, r, on, t, ring, B.lane);
+                    const double at = row_dot<CI, UNR, K, S, STREAM>(P.At, d.sAt, d.row0, 0, q, r, on, t, ring, B.lane);
                     if (on) w[r] = s[r] + at;
                 });
             }
@@ -454,7 +464,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
                 double *__restrict__ f1 = P.f + dn.row0;
                 const double *__restrict__ u1 = P.u + dn.row0;
                 for_slices(B, 0, 0, dn.nBar, [&](int q, int r, bool on) {
-                    const double sv = row_dot<CI, UNR, K, S>(P.R, dn.sR, dn.row0, 0, q, r, on, w, ring, B.lane);
+                    const double sv = row_dot<CI, UNR, K, S, STREAM>(P.R, dn.sR, dn.row0, 0, q, r, on, w, ring, B.lane);
                     if (on) s1[r] = sv;
                     const bool real = on && r < dn.nReal;
                     if (c > 1) {
@@ -463,7 +473,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
                         const bool qa = (q << 5) < dn.nReal;
                         if (qa) {
                             const double au =
-                                row_dot<CI, UNR, K, S>(P.A, dn.sA, dn.row0, 0, q, r, real, u1, ring, B.lane);
+                                row_dot<CI, UNR, K, S, STREAM>(P.A, dn.sA, dn.row0, 0, q, r, real, u1, ring, B.lane);
                             if (real) f1[r] = (f1[r] - au) - sv;
                         }
                     } else if (real) {
@@ -498,12 +508,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
             double *__restrict__ u = P.u + d.row0;
             const double *__restrict__ u1 = P.u + dn.row0;
             for_slices(B, 0, 0, d.nBar, [&](int q, int r, bool on) {
-                const double pu = row_dot<CI, UNR, K, S>(P.P, d.sP, d.row0, 0, q, r, on, u1, ring, B.lane);
+                const double pu = row_dot<CI, UNR, K, S, STREAM>(P.P, d.sP, d.row0, 0, q, r, on, u1, ring, B.lane);
                 if (on) u[r] = u[r] + pu;
             });
             __syncthreads();
-            relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
-            relax_pass<CI, UNR, K, S>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
+            relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
+            relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
         }
     }
 
@@ -576,14 +586,14 @@ cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, doub
     return cudaGetLastError();
 }
 
-template <class CI, int MINB, int UNR, int K, int S, int NT = 512>
+template <class CI, int MINB, int UNR, int K, int S, int NT = 512, bool STREAM = false>
 static cudaError_t launch_variant(const FacParams &P, int nsub, int threads, cudaStream_t st, int *blocks_per_sm)
 {
     if (threads > NT) threads = NT;
     if (NT > 512) threads = NT;
     size_t smem = 0;
     if constexpr (K > 0) smem = (size_t)(threads / 32) * dev::Ring<CI, K, S>::kWarp;
-    auto kern = dev::k_fac_all_grids<CI, MINB, UNR, K, S, NT>;
+    auto kern = dev::k_fac_all_grids<CI, MINB, UNR, K, S, NT, STREAM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -615,7 +625,10 @@ static cudaError_t launch_fac_ci(const FacParams &P, int nsub, int threads, cuda
     case 5: return launch_variant<CI, 4, 2, 2, 4>(P, nsub, threads, st, bps);  // 4 CTAs/SM, cp.async ring 4 x 2
     case 6: return launch_variant<CI, 2, 2, 0, 0, 1024>(P, nsub, threads, st, bps);  // 2 CTAs of 1024/SM
     case 7: return launch_variant<CI, 2, 2, 4, 2, 1024>(P, nsub, threads, st, bps);  // same, cp.async ring 2 x 4
-    default: return launch_variant<CI, 4, 2, 0, 0>(P, nsub, threads, st, bps); // 4 CTAs/SM, 2 entries per step
+    case 8: return launch_variant<CI, 4, 2, 0, 0, 512, true>(P, nsub, threads, st, bps);  // 1 + evict-first operator loads
+    case 9: return launch_variant<CI, 2, 2, 0, 0, 1024, true>(P, nsub, threads, st, bps); // 6 + evict-first operator loads
+    case 1: return launch_variant<CI, 4, 2, 0, 0>(P, nsub, threads, st, bps);  // 4 CTAs/SM, 2 entries per step
+    default: return launch_variant<CI, 4, 2, 0, 0, 512, true>(P, nsub, threads, st, bps);  // schedule 8
     }
 }
 

@@ -161,7 +161,7 @@ def test_no_convergence_status_and_last_iterate():
 
 
 @pytest.mark.parametrize("case", ["poisson3d_24", "ragged2d", "kappa3d"])
-@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_fac_schedules_identical(schedule, case):
     """Every kernel variant (residency, unrolling, cp.async staging depth)
     gives the oracle's bits, states included."""

@@ -226,6 +226,18 @@ def run_reference(args, w):
     print(json.dumps(line))
 
 
+def max_over_ranks(values, dist=None):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest
+    replica sets the whole-job time); identity without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def cpu_baseline(w, iters):
     """Oracle timed on a bounded sample: one full AMG-DD iteration (residual,
     restriction and AlgFAC on every composite grid, OpenMP over grids), scaled
@@ -346,10 +358,7 @@ def main():
     ms_dd = statistics.median(t_dd)
     ms_v = statistics.median(t_v)
     ms_e2e = statistics.median(t_e2e)
-    if dist is not None:
-        tt = torch.tensor([ms_dd, ms_v, ms_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_dd, ms_v, ms_e2e = [float(v) for v in tt.cpu()]
+    ms_dd, ms_v, ms_e2e = max_over_ranks([ms_dd, ms_v, ms_e2e], dist)
     it_dd = i_dd[-1]["iterations"]
     it_v = i_v[-1]["iterations"]
     hbm, peak_kind = _peaks()

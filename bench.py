@@ -132,7 +132,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_fac_bytes(st, nfac, si=2):
+def algorithmic_fac_bytes(st, nfac, si=2, sv=8.0):
     """Bytes one all-grids FAC launch must move: the per-composite-grid formula
     sum_c sum_{l<L} [3 M(A_l real rows) + [c>1] M(A_{l+1} real rows) + 2 M(P_l)
     + 8 * k * |Dbar_l|] summed over grids, with M(X) = nnz*(8 + si) + 4*rows,
@@ -140,7 +140,6 @@ def algorithmic_fac_bytes(st, nfac, si=2):
     level visit. A_l real rows are read by the pre- and post-smoothing sweeps
     and by s_l + A_l t_l; P_l and R_l = P_l^T once each."""
     L = st.num_levels - 1
-    sv = 8.0
 
     def M(nnz, rows):
         return nnz * (sv + si) + 4.0 * rows
@@ -261,6 +260,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--schedule", type=int, default=0, help="FAC kernel variant (0 = library default)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid edge (default 128, the benchmark workload; smaller edges "
@@ -317,6 +317,7 @@ def main():
         clk = ClockSampler(local)
         t_dd, i_dd = timed(s.solve, args.steps)
         clocks = clk.stop()
+        x64 = x.clone()
         barrier()
         timed(s.vcycle_solve, args.warmup)
         t_v, i_v = timed(s.vcycle_solve, args.steps)
@@ -354,6 +355,50 @@ def main():
             e1.synchronize()
             if k >= args.warmup:
                 t_e2e.append(e0.elapsed_time(e1))
+
+    # mixed precision (FP32 AlgFAC inside FP64 refinement) on the same
+    # workload: reported beside the FP64 headline
+    mixed = None
+    if not args.no_mixed:
+        s.close()
+        sm = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                    precision=1, stream=stream)
+        with torch.cuda.stream(stream):
+            def tm(k):
+                ts, inf = [], None
+                for _ in range(k):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    a0 = torch.cuda.Event(enable_timing=True)
+                    a1 = torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    inf = sm.solve(b, x, tol=TOL, max_iter=200, stream=stream)
+                    a1.record(stream)
+                    a1.synchronize()
+                    ts.append(a0.elapsed_time(a1))
+                return ts, inf
+            tm(args.warmup)
+            t_m, i_m = tm(args.steps)
+            capi.amgdd_fac(sm.h, r_all, xf, stream)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(nf):
+                capi.amgdd_fac(sm.h, r_all, xf, stream)
+            a1.record(stream)
+            a1.synchronize()
+            fac_m = a0.elapsed_time(a1) / nf
+        ms_m = max_over_ranks([statistics.median(t_m)], dist)[0]
+        # final error of the mixed solution against the FP64 solution (the
+        # FP64 iterate equals the CPU oracle's bit for bit)
+        err = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
+        mixed = {"ms": round(ms_m, 3), "iterations": i_m["iterations"], "final_relres": i_m["final_relres"],
+                 "rel_error_vs_fp64_solution": err,
+                 "fac_ms_per_launch": round(fac_m, 3),
+                 "fac_gbs_algorithmic_fp32": round(algorithmic_fac_bytes(sm.stats, w["n_fac"], sv=4.0)
+                                                   / (fac_m * 1e-3) / 1e9, 1),
+                 "dtype": "f32 AlgFAC / f64 refinement"}
+        sm.close()
 
     ms_dd = statistics.median(t_dd)
     ms_v = statistics.median(t_v)
@@ -405,12 +450,14 @@ def main():
         "e2e": {"value": round(ms_e2e, 3), "unit": "ms", "h2d_bytes_per_step": 8 * s.n,
                 "d2h_bytes_per_step": 8 * s.n},
         "clocks": clocks,
+        "mixed_precision": mixed,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, it_dd)
     if rank == 0:
         print(json.dumps(line))
-    s.close()
+    if s.h:
+        s.close()
     if dist is not None:
         dist.destroy_process_group()
 

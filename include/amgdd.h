@@ -75,7 +75,12 @@ typedef struct {
                                cp.async rings of different depths; 6, 7 = two
                                blocks of 1024 threads (7 with a cp.async ring);
                                8, 9 = 1 and 6 with evict-first operator loads */
-    int32_t reserved[7];
+    int32_t precision;      /* 0 = FP64 throughout (default); 1 = mixed: AlgFAC
+                               cycles on the composite grids in FP32 (operators
+                               rounded to FP32, fp32 fma chains), inside FP64
+                               iterative refinement: residual, restriction,
+                               coarsest solve and x += u_0 stay FP64 */
+    int32_t reserved[6];
 } amgdd_options;
 
 /* Statistics of a completed setup. */

@@ -1119,8 +1119,173 @@ void orc_amgdd_iteration(void *h, void *c, const double *b, double *x, int nfac,
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Mixed precision: AlgFAC in FP32 inside FP64 iterative refinement     */
+/* ------------------------------------------------------------------ */
+/* The composite-grid cycle of Algorithm 4 with every composite vector and
+ * every operator value rounded to float (round to nearest), fmaf chains over
+ * ascending columns, and the coarsest solve in FP64 on the float right-hand
+ * side (result rounded to float). The global residual, the restriction, the
+ * gather f_l = (float) r_l and the update x += (double) u_0 stay FP64, so the
+ * outer iteration of Algorithm 2 is an iterative refinement whose correction
+ * comes from the FP32 cycles. */
+
+static inline float rowdot32(const Mat *A, int i, const float *x)
+{
+    float s = 0.0f;
+    for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k)
+        s = fmaf((float)A->v[k], x[A->ci[k]], s);
+    return s;
+}
+
+typedef struct {
+    int64_t off[ORC_MAXLEV + 1];
+    float *u, *f, *t, *s, *w, *d;
+} FacWork32;
+
+static void facwork32_init(const Hier *H, FacWork32 *W)
+{
+    W->off[0] = 0;
+    for (int l = 0; l < H->nlev; ++l) W->off[l + 1] = W->off[l] + H->A[l].n;
+    size_t tot = (size_t)W->off[H->nlev];
+    W->u = xcalloc(tot, sizeof(float));
+    W->f = xcalloc(tot, sizeof(float));
+    W->t = xcalloc(tot, sizeof(float));
+    W->s = xcalloc(tot, sizeof(float));
+    W->w = xcalloc(tot, sizeof(float));
+    W->d = xcalloc(tot, sizeof(float));
+}
+
+static void facwork32_free(FacWork32 *W) { free(W->u); free(W->f); free(W->t); free(W->s); free(W->w); free(W->d); }
+
+static void relax_pass32(const Mat *A, const double *l1inv, const int *cf, int which, const int *pts, int npts,
+                         const float *f, float *u, float *t, float *d)
+{
+    for (int q = 0; q < npts; ++q) {
+        int i = pts[q];
+        if (cf[i] != which) continue;
+        d[i] = (f[i] - rowdot32(A, i, u)) * (float)l1inv[i];
+    }
+    for (int q = 0; q < npts; ++q) {
+        int i = pts[q];
+        if (cf[i] != which) continue;
+        u[i] = u[i] + d[i];
+        t[i] = t[i] + d[i];
+    }
+}
+
+static void algfac32(const Hier *H, const Comp *C, int p, const double *rl, int nfac, FacWork32 *W)
+{
+    int L = H->nlev - 1;
+    int nL = H->A[L].n;
+    const CLevel *cl = &C->lv[(size_t)p * C->nlev];
+    for (int l = 0; l <= L; ++l) {
+        float *f = W->f + W->off[l];
+        const double *r = rl + W->off[l];
+        for (int q = 0; q < cl[l].nreal; ++q) f[cl[l].real[q]] = (float)r[cl[l].real[q]];
+    }
+    for (int c = 1; c <= nfac; ++c) {
+        for (int l = 0; l < L; ++l) {
+            const Mat *A = &H->A[l];
+            float *u = W->u + W->off[l], *f = W->f + W->off[l], *t = W->t + W->off[l];
+            float *s = W->s + W->off[l], *w = W->w + W->off[l], *d = W->d + W->off[l];
+            const CLevel *a = &cl[l], *b = &cl[l + 1];
+            if (l != 0) {
+                for (int q = 0; q < a->nreal; ++q) u[a->real[q]] = 0.0f;
+                for (int q = 0; q < a->nghost; ++q) u[a->ghost[q]] = 0.0f;
+            }
+            relax_pass32(A, H->l1inv[l], H->cf[l], 1, a->real, a->nreal, f, u, t, d);
+            relax_pass32(A, H->l1inv[l], H->cf[l], 0, a->real, a->nreal, f, u, t, d);
+            for (int q = 0; q < a->nreal; ++q) { int i = a->real[q]; w[i] = s[i] + rowdot32(A, i, t); }
+            for (int q = 0; q < a->nghost; ++q) { int i = a->ghost[q]; w[i] = s[i] + rowdot32(A, i, t); }
+            float *s1 = W->s + W->off[l + 1], *f1 = W->f + W->off[l + 1], *u1 = W->u + W->off[l + 1];
+            for (int q = 0; q < b->nreal; ++q) { int I = b->real[q]; s1[I] = rowdot32(&H->R[l], I, w); }
+            for (int q = 0; q < b->nghost; ++q) { int I = b->ghost[q]; s1[I] = rowdot32(&H->R[l], I, w); }
+            if (c > 1)
+                for (int q = 0; q < b->nreal; ++q) { int I = b->real[q]; f1[I] = f1[I] - rowdot32(&H->A[l + 1], I, u1); }
+            for (int q = 0; q < b->nreal; ++q) { int I = b->real[q]; f1[I] = f1[I] - s1[I]; }
+            for (int q = 0; q < a->nreal; ++q) { int i = a->real[q]; t[i] = 0.0f; s[i] = 0.0f; w[i] = 0.0f; }
+            for (int q = 0; q < a->nghost; ++q) { int i = a->ghost[q]; t[i] = 0.0f; s[i] = 0.0f; w[i] = 0.0f; }
+        }
+        {
+            const float *f = W->f + W->off[L];
+            float *u = W->u + W->off[L];
+            for (int I = 0; I < nL; ++I) {
+                double acc = 0.0;
+                for (int J = 0; J < nL; ++J) acc = fma(H->ainv[(size_t)I * nL + J], (double)f[J], acc);
+                u[I] = (float)acc;
+            }
+        }
+        for (int l = L - 1; l >= 0; --l) {
+            const Mat *A = &H->A[l];
+            float *u = W->u + W->off[l], *f = W->f + W->off[l], *t = W->t + W->off[l], *d = W->d + W->off[l];
+            const float *u1 = W->u + W->off[l + 1];
+            const CLevel *a = &cl[l];
+            for (int q = 0; q < a->nreal; ++q) { int i = a->real[q]; u[i] = u[i] + rowdot32(&H->P[l], i, u1); }
+            for (int q = 0; q < a->nghost; ++q) { int i = a->ghost[q]; u[i] = u[i] + rowdot32(&H->P[l], i, u1); }
+            relax_pass32(A, H->l1inv[l], H->cf[l], 0, a->real, a->nreal, f, u, t, d);
+            relax_pass32(A, H->l1inv[l], H->cf[l], 1, a->real, a->nreal, f, u, t, d);
+        }
+    }
+}
+
+static void facwork32_clear(const Hier *H, const Comp *C, int p, FacWork32 *W)
+{
+    const CLevel *cl = &C->lv[(size_t)p * C->nlev];
+    for (int l = 0; l < H->nlev; ++l) {
+        int64_t o = W->off[l];
+        for (int pass = 0; pass < 2; ++pass) {
+            const int *set = pass ? cl[l].ghost : cl[l].real;
+            int ns = pass ? cl[l].nghost : cl[l].nreal;
+            for (int q = 0; q < ns; ++q) {
+                int64_t i = o + set[q];
+                W->u[i] = 0.0f; W->f[i] = 0.0f; W->t[i] = 0.0f; W->s[i] = 0.0f; W->w[i] = 0.0f; W->d[i] = 0.0f;
+            }
+        }
+    }
+}
+
+/* FP32 AlgFAC on one composite grid; outputs widened to double, levels back
+ * to back, global indexing, zero outside the grid. */
+void orc_algfac32(void *h, void *c, int p, const double *rl, int nfac, double *u_out, double *f_out)
+{
+    Hier *H = h;
+    FacWork32 W;
+    facwork32_init(H, &W);
+    algfac32(H, c, p, rl, nfac, &W);
+    int64_t tot = W.off[H->nlev];
+    for (int64_t i = 0; i < tot; ++i) { u_out[i] = W.u[i]; f_out[i] = W.f[i]; }
+    facwork32_free(&W);
+}
+
+/* One mixed-precision AMG-DD iteration (Algorithm 2 with FP32 AlgFAC). */
+void orc_amgdd_iteration32(void *h, void *c, const double *b, double *x, int nfac, double *rl)
+{
+    Hier *H = h;
+    Comp *C = c;
+    orc_residual(h, b, x, rl);
+    orc_restrict_all(h, rl);
+#pragma omp parallel
+    {
+        FacWork32 W;
+        facwork32_init(H, &W);
+#pragma omp for schedule(dynamic, 1)
+        for (int p = 0; p < C->nsub; ++p) {
+            algfac32(H, C, p, rl, nfac, &W);
+            const CLevel *c0 = &C->lv[(size_t)p * C->nlev];
+            for (int q = 0; q < c0->nowned; ++q) {
+                int i = c0->owned[q];
+                x[i] = x[i] + (double)W.u[i];
+            }
+            facwork32_clear(H, C, p, &W);
+        }
+        facwork32_free(&W);
+    }
+}
+
 /* AMG-DD solver: iterations of Algorithm 2 until ||b - A x|| / ||b|| <= tol. */
-int orc_amgdd_solve(void *h, void *c, const double *b, double *x, double tol, int maxit, int nfac, double *hist)
+int orc_amgdd_solve(void *h, void *c, const double *b, double *x, double tol, int maxit, int nfac, int mixed,
+                    double *hist)
 {
     Hier *H = h;
     int n = H->A[0].n;
@@ -1135,7 +1300,8 @@ int orc_amgdd_solve(void *h, void *c, const double *b, double *x, double tol, in
         double rel = ref > 0.0 ? nr / ref : 0.0;
         hist[k] = rel;
         if (rel <= tol || k >= maxit) break;
-        orc_amgdd_iteration(h, c, b, x, nfac, NULL, -1, rl);
+        if (mixed) orc_amgdd_iteration32(h, c, b, x, nfac, rl);
+        else orc_amgdd_iteration(h, c, b, x, nfac, NULL, -1, rl);
         ++k;
     }
     free(rl);

@@ -72,7 +72,9 @@ def oracle_lib():
             "orc_algfac": (None, [vp, vp, C.c_int, f64p, C.c_int, f64p, f64p]),
             "orc_masked_fac": (None, [vp, vp, C.c_int, f64p, C.c_int, f64p, f64p]),
             "orc_amgdd_iteration": (None, [vp, vp, f64p, f64p, C.c_int, i32p, C.c_int, f64p]),
-            "orc_amgdd_solve": (C.c_int, [vp, vp, f64p, f64p, C.c_double, C.c_int, C.c_int, f64p]),
+            "orc_amgdd_solve": (C.c_int, [vp, vp, f64p, f64p, C.c_double, C.c_int, C.c_int, C.c_int, f64p]),
+            "orc_algfac32": (None, [vp, vp, C.c_int, f64p, C.c_int, f64p, f64p]),
+            "orc_amgdd_iteration32": (None, [vp, vp, f64p, f64p, C.c_int, f64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -242,9 +244,24 @@ class Oracle:
         self.lib.orc_amgdd_iteration(self.h, self.c, _c64(b), x, int(nfac), sel, ns, rl)
         return x
 
-    def amgdd_solve(self, b, nfac, x0=None, tol=1e-8, maxit=200):
+    def amgdd_solve(self, b, nfac, x0=None, tol=1e-8, maxit=200, mixed=False):
+        """Algorithm 2 to tol; mixed=True runs the AlgFAC cycles in FP32."""
         x = np.zeros(self.n) if x0 is None else _c64(x0).copy()
         hist = np.zeros(maxit + 1)
         k = self.lib.orc_amgdd_solve(self.h, self.c, _c64(b), x, float(tol), int(maxit),
-                                     int(nfac), hist)
+                                     int(nfac), int(bool(mixed)), hist)
         return x, hist[:k + 1]
+
+    def algfac32(self, p, rl, nfac):
+        """FP32 AlgFAC on composite grid p (values widened to double)."""
+        flat = _c64(np.concatenate(rl))
+        u = np.zeros(int(self.offsets[-1]))
+        f = np.zeros(int(self.offsets[-1]))
+        self.lib.orc_algfac32(self.h, self.c, int(p), flat, int(nfac), u, f)
+        return self._split(u), self._split(f)
+
+    def amgdd_iteration32(self, b, x, nfac):
+        x = _c64(x).copy()
+        rl = np.zeros(int(self.offsets[-1]))
+        self.lib.orc_amgdd_iteration32(self.h, self.c, _c64(b), x, int(nfac), rl)
+        return x

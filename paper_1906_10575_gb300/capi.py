@@ -34,7 +34,8 @@ class amgdd_csr(C.Structure):
 class amgdd_options(C.Structure):
     _fields_ = [("theta", C.c_double), ("max_coarse", C.c_int32), ("max_levels", C.c_int32),
                 ("n_fac", C.c_int32), ("strict_assumption", C.c_int32), ("host_only", C.c_int32),
-                ("threads", C.c_int32), ("schedule", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("threads", C.c_int32), ("schedule", C.c_int32), ("precision", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class amgdd_setup_stats(C.Structure):

@@ -228,6 +228,7 @@ amgdd_status amgdd_options_default(amgdd_options *o)
     o->host_only = 0;
     o->threads = 0;
     o->schedule = 0;
+    o->precision = 0;
     return AMGDD_OK;
 }
 
@@ -280,7 +281,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
     if (opts) h->opt = *opts;
     else amgdd_options_default(&h->opt);
     if (h->opt.n_fac < 1 || h->opt.max_levels < 1 || h->opt.max_coarse < 1 || !(h->opt.theta > 0.0) ||
-        !(h->opt.theta <= 1.0)) {
+        !(h->opt.theta <= 1.0) || h->opt.precision < 0 || h->opt.precision > 1) {
         delete h;
         return fail(nullptr, AMGDD_ERR_INVALID_ARG, "options out of range");
     }
@@ -350,7 +351,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             S.fac_fma = 0;
             for (int p = 0; p < nsub; ++p)
                 S.fac_fma += F.work1[p] + (int64_t)(h->opt.n_fac - 1) * F.work[p];
-            S.fac_entry_bytes = 8 + (F.max_bar < 65536 ? 2 : 4);
+            S.fac_entry_bytes = (h->opt.precision == 1 ? 4 : 8) + (F.max_bar < 65536 ? 2 : 4);
             // stored entries of the local operators (padding excluded)
             for (int l = 0; l < nlev; ++l) {
                 S.comp_nnz_A[l] = F.lvA[l];
@@ -420,7 +421,18 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             if ((e = upload(h, F.desc, &dd, st_)) != cudaSuccess) return bail(e, "upload desc");
             if ((e = upload(h, F.order, &ord, st_)) != cudaSuccess) return bail(e, "upload order");
             if ((e = upload(h, F.gmap, &gm, st_)) != cudaSuccess) return bail(e, "upload gmap");
-            if ((e = upload(h, F.l1inv, &l1, st_)) != cudaSuccess) return bail(e, "upload l1inv");
+            const bool fp32 = h->opt.precision == 1;
+            P.fp32 = fp32 ? 1 : 0;
+            if (fp32) {
+                std::vector<float> l1f(F.l1inv.begin(), F.l1inv.end());
+                float *l1d;
+                if ((e = upload(h, l1f, &l1d, st_)) != cudaSuccess) return bail(e, "upload l1inv");
+                if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload l1inv");
+                l1 = nullptr;
+                P.l1inv = l1d;
+            } else {
+                if ((e = upload(h, F.l1inv, &l1, st_)) != cudaSuccess) return bail(e, "upload l1inv");
+            }
             if ((e = upload(h, F.owned, &own, st_)) != cudaSuccess) return bail(e, "upload owned");
             if ((e = upload(h, F.owned0, &o0, st_)) != cudaSuccess) return bail(e, "upload owned0");
             P.col16 = F.max_bar < 65536 ? 1 : 0;
@@ -431,10 +443,20 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
                 FacView &V = *views[v];
                 int64_t *so;
                 uint16_t *rl;
-                double *va;
+                const void *va;
                 if ((e = upload(h, V.soff, &so, st_)) != cudaSuccess) return bail(e, "upload view slices");
                 if ((e = upload(h, V.rlen, &rl, st_)) != cudaSuccess) return bail(e, "upload view rows");
-                if ((e = upload(h, V.val, &va, st_)) != cudaSuccess) return bail(e, "upload view values");
+                if (fp32) {
+                    std::vector<float> vf(V.val.begin(), V.val.end());   // round to nearest FP32
+                    float *vd;
+                    if ((e = upload(h, vf, &vd, st_)) != cudaSuccess) return bail(e, "upload view values");
+                    if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload view values");
+                    va = vd;
+                } else {
+                    double *vd;
+                    if ((e = upload(h, V.val, &vd, st_)) != cudaSuccess) return bail(e, "upload view values");
+                    va = vd;
+                }
                 const void *co;
                 if (P.col16) {
                     std::vector<uint16_t> c16(V.col.begin(), V.col.end());
@@ -487,14 +509,23 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             P.desc = dd;
             P.order = ord;
             P.gmap = gm;
-            P.l1inv = l1;
+            if (!fp32) P.l1inv = l1;
             P.owned = own;
             P.owned0 = o0;
             P.ainv = h->ainv;
             for (int l = 0; l <= kMaxLevels; ++l) P.level_off[l] = l <= nlev ? h->level_off[l] : 0;
-            double *ws[6];
-            for (int k = 0; k < 6; ++k)
-                if ((e = alloc(h, (size_t)F.rows_total, &ws[k])) != cudaSuccess) return bail(e, "alloc FAC workspace");
+            void *ws[6];
+            for (int k = 0; k < 6; ++k) {
+                if (fp32) {
+                    float *w;
+                    if ((e = alloc(h, (size_t)F.rows_total, &w)) != cudaSuccess) return bail(e, "alloc FAC workspace");
+                    ws[k] = w;
+                } else {
+                    double *w;
+                    if ((e = alloc(h, (size_t)F.rows_total, &w)) != cudaSuccess) return bail(e, "alloc FAC workspace");
+                    ws[k] = w;
+                }
+            }
             P.u = ws[0]; P.f = ws[1]; P.t = ws[2]; P.s = ws[3]; P.w = ws[4]; P.d = ws[5];
             if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "setup upload");
             h->desc = F.desc;
@@ -698,8 +729,20 @@ amgdd_status amgdd_get_fac_state(amgdd_handle h, int32_t sub, int32_t level, dou
     std::vector<double> hu((size_t)d.nBar), hf((size_t)d.nBar);
     cudaStream_t st = h->last_stream;
     CK(cudaStreamSynchronize(st), "sync");
-    CK(cudaMemcpy(hu.data(), h->fac.u + d.row0, sizeof(double) * (size_t)d.nBar, cudaMemcpyDeviceToHost), "copy u");
-    CK(cudaMemcpy(hf.data(), h->fac.f + d.row0, sizeof(double) * (size_t)d.nBar, cudaMemcpyDeviceToHost), "copy f");
+    if (h->fac.fp32) {
+        std::vector<float> fu((size_t)d.nBar), ff((size_t)d.nBar);
+        CK(cudaMemcpy(fu.data(), static_cast<float *>(h->fac.u) + d.row0, sizeof(float) * (size_t)d.nBar,
+                      cudaMemcpyDeviceToHost), "copy u");
+        CK(cudaMemcpy(ff.data(), static_cast<float *>(h->fac.f) + d.row0, sizeof(float) * (size_t)d.nBar,
+                      cudaMemcpyDeviceToHost), "copy f");
+        hu.assign(fu.begin(), fu.end());
+        hf.assign(ff.begin(), ff.end());
+    } else {
+        CK(cudaMemcpy(hu.data(), static_cast<double *>(h->fac.u) + d.row0, sizeof(double) * (size_t)d.nBar,
+                      cudaMemcpyDeviceToHost), "copy u");
+        CK(cudaMemcpy(hf.data(), static_cast<double *>(h->fac.f) + d.row0, sizeof(double) * (size_t)d.nBar,
+                      cudaMemcpyDeviceToHost), "copy f");
+    }
     for (int32_t r = 0; r < d.nBar; ++r) {
         const int32_t m = h->dev2map[d.row0 + r];
         if (u) u[m] = hu[r];

@@ -174,35 +174,37 @@ struct Block {
     int lane, warp, nw, tid, nt;
 };
 
-// Row product of local row `r` of a composite-grid view whose slices start at
-// local row `first`: slice q = (r - first) / 32, lane = (r - first) % 32.
 // Loads of operator entries, which every launch streams once: evict-first
 // (ld.global.cs) when STREAM is set, so they do not push the composite-grid
 // vectors out of L2; read-only path (ld.global.nc) otherwise.
-template <bool STREAM, class T>
-__device__ __forceinline__ T ld_op(const T *p)
+template <bool STREAM, class X>
+__device__ __forceinline__ X ld_op(const X *p)
 {
     if constexpr (STREAM) return __ldcs(p);
     else return __ldg(p);
 }
 
-template <class CI, int UNR, bool STREAM = false>
-__device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int r,
-                                           const double *__restrict__ x)
+// Row product of local row `r` of a composite-grid view whose slices start at
+// local row `first`: slice q = (r - first) / 32, lane = (r - first) % 32. T is
+// the arithmetic type of the composite grid (double, or float in the mixed-
+// precision mode): s = 0; s = fma(a_k, x_k, s) in T over ascending entries.
+template <class CI, int UNR, bool STREAM = false, class T = double>
+__device__ __forceinline__ T view_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int r,
+                                      const T *__restrict__ x)
 {
     const int v = r - first;
     const int64_t base = __ldg(V.soff + slice0 + (v >> 5)) + (v & 31);
     const int len = __ldg(V.rlen + row0 + r);
     const CI *__restrict__ c = static_cast<const CI *>(V.col) + base;
-    const double *__restrict__ a = V.val + base;
-    double s = 0.0;
+    const T *__restrict__ a = static_cast<const T *>(V.val) + base;
+    T s = T(0);
     int k = 0;
     if constexpr (UNR == 2) {
 #pragma unroll 1
         for (; k + 2 <= len; k += 2) {
             const int c0 = ld_op<STREAM>(c + 32 * k), c1 = ld_op<STREAM>(c + 32 * (k + 1));
-            const double a0 = ld_op<STREAM>(a + 32 * k), a1 = ld_op<STREAM>(a + 32 * (k + 1));
-            const double x0 = x[c0], x1 = x[c1];
+            const T a0 = ld_op<STREAM>(a + 32 * k), a1 = ld_op<STREAM>(a + 32 * (k + 1));
+            const T x0 = x[c0], x1 = x[c1];
             s = fma(a0, x0, s);
             s = fma(a1, x1, s);
         }
@@ -210,20 +212,20 @@ __device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, 
         return s;
     } else {
 #pragma unroll 1
-    for (; k + UNR <= len; k += UNR) {
-        int ci[UNR];
-        double av[UNR], xv[UNR];
+        for (; k + UNR <= len; k += UNR) {
+            int ci[UNR];
+            T av[UNR], xv[UNR];
 #pragma unroll
-        for (int j = 0; j < UNR; ++j) ci[j] = ld_op<STREAM>(c + 32 * (k + j));
+            for (int j = 0; j < UNR; ++j) ci[j] = ld_op<STREAM>(c + 32 * (k + j));
 #pragma unroll
-        for (int j = 0; j < UNR; ++j) av[j] = ld_op<STREAM>(a + 32 * (k + j));
+            for (int j = 0; j < UNR; ++j) av[j] = ld_op<STREAM>(a + 32 * (k + j));
 #pragma unroll
-        for (int j = 0; j < UNR; ++j) xv[j] = x[ci[j]];
+            for (int j = 0; j < UNR; ++j) xv[j] = x[ci[j]];
 #pragma unroll
-        for (int j = 0; j < UNR; ++j) s = fma(av[j], xv[j], s);
-    }
-    for (; k < len; ++k) s = fma(ld_op<STREAM>(a + 32 * k), x[ld_op<STREAM>(c + 32 * k)], s);
-    return s;
+            for (int j = 0; j < UNR; ++j) s = fma(av[j], xv[j], s);
+        }
+        for (; k < len; ++k) s = fma(ld_op<STREAM>(a + 32 * k), x[ld_op<STREAM>(c + 32 * k)], s);
+        return s;
     }
 }
 
@@ -231,7 +233,7 @@ __device__ __forceinline__ double view_dot(const FacViewDev &V, int64_t slice0, 
 // Each warp owns a ring of S stages; a stage holds K consecutive k-steps of the
 // slice being multiplied: K x 32 values, then K x 32 column indices. The
 // copies hold no registers while in flight, so a lane can keep S*K entries
-// outstanding within the 32-register budget.
+// outstanding within the 32-register budget. (FP64 composite grids only.)
 template <class CI, int K, int S>
 struct Ring {
     static constexpr int kVal = K * 32 * 8;
@@ -279,7 +281,7 @@ __device__ __forceinline__ double view_dot_async(const FacViewDev &V, int64_t sl
     using R = Ring<CI, K, S>;
     const int64_t a = __ldg(V.soff + slice), b = __ldg(V.soff + slice + 1);
     const int W = (int)((b - a) >> 5);
-    const double *gval = V.val + a;
+    const double *gval = static_cast<const double *>(V.val) + a;
     const CI *gcol = static_cast<const CI *>(V.col) + a;
 #pragma unroll
     for (int c = 0; c < S - 1; ++c) issue_chunk<CI, K, S>(ring, gval, gcol, W, c, lane);
@@ -334,45 +336,47 @@ __device__ __forceinline__ void for_slices(const Block &B, int first, int r0, in
 }
 
 // Row product of local row r of a view: direct loads (K == 0) or staged
-// through the warp's cp.async ring (K > 0). `active` rows only accumulate.
-template <class CI, int UNR, int K, int S, bool STREAM = false>
-__device__ __forceinline__ double row_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int q, int r,
-                                          bool active, const double *__restrict__ x, unsigned char *ring, int lane)
+// through the warp's cp.async ring (K > 0, FP64 only). `active` rows only
+// accumulate.
+template <class CI, int UNR, int K, int S, bool STREAM, class T>
+__device__ __forceinline__ T row_dot(const FacViewDev &V, int64_t slice0, int64_t row0, int first, int q, int r,
+                                     bool active, const T *__restrict__ x, unsigned char *ring, int lane)
 {
     if constexpr (K == 0) {
-        return active ? view_dot<CI, UNR, STREAM>(V, slice0, row0, first, r, x) : 0.0;
+        return active ? view_dot<CI, UNR, STREAM, T>(V, slice0, row0, first, r, x) : T(0);
     } else {
+        static_assert(sizeof(T) == 8, "cp.async staging is built for FP64 composite grids");
         const int len = active ? (int)__ldg(V.rlen + row0 + r) : 0;
         return view_dot_async<CI, K, S>(V, slice0 + q, len, lane, x, ring);
     }
 }
 
 // One Jacobi half-sweep over local rows [r0, r1) with view V (slices from
-// `first`): d = (f - V u) / l1 for every row, then u += d, t += d.
-template <class CI, int UNR, int K, int S, bool STREAM>
+// `first`): d = (f - V u) * (1/l1) for every row, then u += d, t += d.
+template <class CI, int UNR, int K, int S, bool STREAM, class T>
 __device__ __forceinline__ void relax_pass(const FacParams &P, const Block &B, const FacLevelDesc &d,
                                            const FacViewDev &V, int64_t s0, int first, int r0, int r1,
                                            unsigned char *ring)
 {
-    double *__restrict__ u = P.u + d.row0;
-    double *__restrict__ t = P.t + d.row0;
-    double *__restrict__ dd = P.d + d.row0;
-    const double *__restrict__ f = P.f + d.row0;
-    const double *__restrict__ l1 = P.l1inv + d.row0;
+    T *__restrict__ u = static_cast<T *>(P.u) + d.row0;
+    T *__restrict__ t = static_cast<T *>(P.t) + d.row0;
+    T *__restrict__ dd = static_cast<T *>(P.d) + d.row0;
+    const T *__restrict__ f = static_cast<const T *>(P.f) + d.row0;
+    const T *__restrict__ l1 = static_cast<const T *>(P.l1inv) + d.row0;
     for_slices(B, first, r0, r1, [&](int q, int r, bool on) {
-        const double s = row_dot<CI, UNR, K, S, STREAM>(V, s0, d.row0, first, q, r, on, u, ring, B.lane);
+        const T s = row_dot<CI, UNR, K, S, STREAM, T>(V, s0, d.row0, first, q, r, on, u, ring, B.lane);
         if (on) dd[r] = (f[r] - s) * l1[r];
     });
     __syncthreads();
     for_rows(B, first, r0, r1, [&](int r) {
-        const double v = dd[r];
+        const T v = dd[r];
         u[r] = u[r] + v;
         t[r] = t[r] + v;
     });
     __syncthreads();
 }
 
-template <class CI, int MINB, int UNR, int K, int S, int NT = 512, bool STREAM = false>
+template <class CI, int MINB, int UNR, int K, int S, int NT = 512, bool STREAM = false, class T = double>
 __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
 {
     extern __shared__ __align__(16) unsigned char fac_smem[];
@@ -383,6 +387,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
     B.warp = threadIdx.x >> 5;
     B.nw = blockDim.x >> 5;
     unsigned char *ring = K > 0 ? fac_smem + (size_t)B.warp * Ring<CI, (K > 0 ? K : 1), (S > 0 ? S : 1)>::kWarp : nullptr;
+    T *__restrict__ Pu = static_cast<T *>(P.u);
+    T *__restrict__ Pf = static_cast<T *>(P.f);
+    T *__restrict__ Pt = static_cast<T *>(P.t);
+    T *__restrict__ Ps = static_cast<T *>(P.s);
+    T *__restrict__ Pw = static_cast<T *>(P.w);
+    const T *__restrict__ Pl1 = static_cast<const T *>(P.l1inv);
     __shared__ int claimed;
     for (;;) {
     // claim the next grid: own SM's bin first, then the others (each probe
@@ -410,10 +420,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
         const double *__restrict__ rl = P.r_all + P.level_off[l];
         for (int r = B.tid; r < d.nBar; r += B.nt) {
             const int64_t i = d.row0 + r;
-            P.u[i] = 0.0;
-            P.t[i] = 0.0;
-            P.s[i] = 0.0;
-            if (r < d.nReal) P.f[i] = rl[P.gmap[i]];
+            Pu[i] = T(0);
+            Pt[i] = T(0);
+            Ps[i] = T(0);
+            if (r < d.nReal) Pf[i] = (T)rl[P.gmap[i]];
         }
     }
     __syncthreads();
@@ -424,34 +434,34 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
             const FacLevelDesc dn = D[l + 1];
             if (l > 0) {
                 // u_l <- 0, then the C half-sweep, which with u = 0 is
-                // delta = (f - 0) / l1; the F half-sweep then only sees the
+                // delta = (f - 0) * (1/l1); the F half-sweep then only sees the
                 // C values of u (view AFc)
-                double *__restrict__ u = P.u + d.row0;
-                double *__restrict__ t = P.t + d.row0;
-                const double *__restrict__ f = P.f + d.row0;
-                const double *__restrict__ l1 = P.l1inv + d.row0;
+                T *__restrict__ u = Pu + d.row0;
+                T *__restrict__ t = Pt + d.row0;
+                const T *__restrict__ f = Pf + d.row0;
+                const T *__restrict__ l1 = Pl1 + d.row0;
                 for (int r = B.tid; r < d.nBar; r += B.nt) {
                     if (r < d.nC) {
-                        const double v = f[r] * l1[r];
-                        u[r] = 0.0 + v;
+                        const T v = f[r] * l1[r];
+                        u[r] = T(0) + v;
                         t[r] = t[r] + v;
                     } else {
-                        u[r] = 0.0;
+                        u[r] = T(0);
                     }
                 }
                 __syncthreads();
-                relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, ring);
+                relax_pass<CI, UNR, K, S, STREAM, T>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, ring);
             } else {
-                relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
-                relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
+                relax_pass<CI, UNR, K, S, STREAM, T>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
+                relax_pass<CI, UNR, K, S, STREAM, T>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
             }
             // w_l = s_l + A_l t_l on Dbar_l (t_l is zero off the real points)
             {
-                const double *__restrict__ t = P.t + d.row0;
-                const double *__restrict__ s = P.s + d.row0;
-                double *__restrict__ w = P.w + d.row0;
+                const T *__restrict__ t = Pt + d.row0;
+                const T *__restrict__ s = Ps + d.row0;
+                T *__restrict__ w = Pw + d.row0;
                 for_slices(B, 0, 0, d.nBar, [&](int q, int r, bool on) {
-                    const double at = row_dot<CI, UNR, K, S, STREAM>(P.At, d.sAt, d.row0, 0, q, r, on, t, ring, B.lane);
+                    const T at = row_dot<CI, UNR, K, S, STREAM, T>(P.At, d.sAt, d.row0, 0, q, r, on, t, ring, B.lane);
                     if (on) w[r] = s[r] + at;
                 });
             }
@@ -459,12 +469,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
             // s_{l+1} = R_l w_l on Dbar_{l+1}; f_{l+1} -= A_{l+1} u_{l+1} (c > 1);
             // f_{l+1} -= s_{l+1}; then t_l = s_l = 0
             {
-                const double *__restrict__ w = P.w + d.row0;
-                double *__restrict__ s1 = P.s + dn.row0;
-                double *__restrict__ f1 = P.f + dn.row0;
-                const double *__restrict__ u1 = P.u + dn.row0;
+                const T *__restrict__ w = Pw + d.row0;
+                T *__restrict__ s1 = Ps + dn.row0;
+                T *__restrict__ f1 = Pf + dn.row0;
+                const T *__restrict__ u1 = Pu + dn.row0;
                 for_slices(B, 0, 0, dn.nBar, [&](int q, int r, bool on) {
-                    const double sv = row_dot<CI, UNR, K, S, STREAM>(P.R, dn.sR, dn.row0, 0, q, r, on, w, ring, B.lane);
+                    const T sv = row_dot<CI, UNR, K, S, STREAM, T>(P.R, dn.sR, dn.row0, 0, q, r, on, w, ring, B.lane);
                     if (on) s1[r] = sv;
                     const bool real = on && r < dn.nReal;
                     if (c > 1) {
@@ -472,48 +482,48 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
                         // past them have no row
                         const bool qa = (q << 5) < dn.nReal;
                         if (qa) {
-                            const double au =
-                                row_dot<CI, UNR, K, S, STREAM>(P.A, dn.sA, dn.row0, 0, q, r, real, u1, ring, B.lane);
+                            const T au =
+                                row_dot<CI, UNR, K, S, STREAM, T>(P.A, dn.sA, dn.row0, 0, q, r, real, u1, ring, B.lane);
                             if (real) f1[r] = (f1[r] - au) - sv;
                         }
                     } else if (real) {
                         f1[r] = f1[r] - sv;
                     }
                 });
-                double *__restrict__ t = P.t + d.row0;
-                double *__restrict__ s = P.s + d.row0;
+                T *__restrict__ t = Pt + d.row0;
+                T *__restrict__ s = Ps + d.row0;
                 for (int r = B.tid; r < d.nBar; r += B.nt) {
-                    t[r] = 0.0;
-                    s[r] = 0.0;
+                    t[r] = T(0);
+                    s[r] = T(0);
                 }
             }
             __syncthreads();
         }
-        // coarsest level: u_L = A_L^{-1} f_L (local order = global order)
+        // coarsest level: u_L = A_L^{-1} f_L in FP64 (local order = global order)
         {
             const FacLevelDesc d = D[L];
-            const double *__restrict__ f = P.f + d.row0;
-            double *__restrict__ u = P.u + d.row0;
+            const T *__restrict__ f = Pf + d.row0;
+            T *__restrict__ u = Pu + d.row0;
             for (int I = B.tid; I < P.nL; I += B.nt) {
                 double s = 0.0;
                 const double *__restrict__ a = P.ainv + (int64_t)I * P.nL;
-                for (int J = 0; J < P.nL; ++J) s = fma(__ldg(a + J), f[J], s);
-                u[I] = s;
+                for (int J = 0; J < P.nL; ++J) s = fma(__ldg(a + J), (double)f[J], s);
+                u[I] = (T)s;
             }
         }
         __syncthreads();
         for (int l = L - 1; l >= 0; --l) {
             const FacLevelDesc d = D[l];
             const FacLevelDesc dn = D[l + 1];
-            double *__restrict__ u = P.u + d.row0;
-            const double *__restrict__ u1 = P.u + dn.row0;
+            T *__restrict__ u = Pu + d.row0;
+            const T *__restrict__ u1 = Pu + dn.row0;
             for_slices(B, 0, 0, d.nBar, [&](int q, int r, bool on) {
-                const double pu = row_dot<CI, UNR, K, S, STREAM>(P.P, d.sP, d.row0, 0, q, r, on, u1, ring, B.lane);
+                const T pu = row_dot<CI, UNR, K, S, STREAM, T>(P.P, d.sP, d.row0, 0, q, r, on, u1, ring, B.lane);
                 if (on) u[r] = u[r] + pu;
             });
             __syncthreads();
-            relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
-            relax_pass<CI, UNR, K, S, STREAM>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
+            relax_pass<CI, UNR, K, S, STREAM, T>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal, ring);
+            relax_pass<CI, UNR, K, S, STREAM, T>(P, B, d, P.A, d.sA, 0, 0, d.nC, ring);
         }
     }
 
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fac_all_grids(FacParams P)
     for (int64_t k = o0 + B.tid; k < o1; k += B.nt) {
         const int64_t i = d0.row0 + P.owned[k];
         const int32_t g = P.gmap[i];
-        P.x[g] = P.x[g] + P.u[i];
+        P.x[g] = P.x[g] + (double)Pu[i];
     }
     }
 }
@@ -586,14 +596,14 @@ cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, doub
     return cudaGetLastError();
 }
 
-template <class CI, int MINB, int UNR, int K, int S, int NT = 512, bool STREAM = false>
+template <class CI, int MINB, int UNR, int K, int S, int NT = 512, bool STREAM = false, class T = double>
 static cudaError_t launch_variant(const FacParams &P, int nsub, int threads, cudaStream_t st, int *blocks_per_sm)
 {
     if (threads > NT) threads = NT;
     if (NT > 512) threads = NT;
     size_t smem = 0;
     if constexpr (K > 0) smem = (size_t)(threads / 32) * dev::Ring<CI, K, S>::kWarp;
-    auto kern = dev::k_fac_all_grids<CI, MINB, UNR, K, S, NT, STREAM>;
+    auto kern = dev::k_fac_all_grids<CI, MINB, UNR, K, S, NT, STREAM, T>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -618,6 +628,10 @@ static cudaError_t launch_variant(const FacParams &P, int nsub, int threads, cud
 template <class CI>
 static cudaError_t launch_fac_ci(const FacParams &P, int nsub, int threads, cudaStream_t st, int *bps)
 {
+    if (P.fp32) {  // FP32 composite grids: direct-load schedules only
+        if (P.schedule == 1) return launch_variant<CI, 4, 2, 0, 0, 512, false, float>(P, nsub, threads, st, bps);
+        return launch_variant<CI, 4, 2, 0, 0, 512, true, float>(P, nsub, threads, st, bps);
+    }
     switch (P.schedule) {
     case 2: return launch_variant<CI, 3, 4, 0, 0>(P, nsub, threads, st, bps);  // 3 CTAs/SM, 4 entries per step
     case 3: return launch_variant<CI, 4, 2, 4, 2>(P, nsub, threads, st, bps);  // 4 CTAs/SM, cp.async ring 2 x 4

@@ -39,7 +39,7 @@ struct FacViewDev {
     const int64_t *soff;
     const uint16_t *rlen;
     const void *col;
-    const double *val;
+    const void *val;            // double or float (the composite grid's type)
 };
 
 constexpr int kMaxLevels = 40;
@@ -58,7 +58,7 @@ struct FacParams {
     const FacLevelDesc *desc;   // [p * nlev + l]
     const int32_t *order;       // launch order of the grids
     const int32_t *gmap;        // per row: level index
-    const double *l1inv;        // per row
+    const void *l1inv;          // per row, composite grid's type
     FacViewDev A, At, AFc, P, R;
     const int32_t *owned;       // level-0 local indices of owned points
     const int64_t *owned0;      // per grid offset (nsub + 1)
@@ -66,7 +66,8 @@ struct FacParams {
     const double *r_all;        // restricted residuals, levels back to back
     int64_t level_off[kMaxLevels + 1];
     double *x;
-    double *u, *f, *t, *s, *w, *d;  // per-row workspace
+    void *u, *f, *t, *s, *w, *d;    // per-row workspace, composite grid's type
+    int fp32;                   // 1: composite grids in FP32 (mixed precision)
 };
 
 cudaError_t launch_residual(const SellView &A, const double *b, const double *x, double *r, double *partial,

@@ -14,7 +14,8 @@ class Solver:
     """
 
     def __init__(self, rowptr, col, val, part, nsub, padding=1, n_fac=2, theta=0.25,
-                 max_coarse=16, max_levels=25, host_only=False, threads=0, schedule=0, stream=None):
+                 max_coarse=16, max_levels=25, host_only=False, threads=0, schedule=0, precision=0,
+                 stream=None):
         o = capi.amgdd_options_default()
         o.n_fac = n_fac
         o.theta = theta
@@ -23,6 +24,7 @@ class Solver:
         o.host_only = int(host_only)
         o.threads = threads
         o.schedule = schedule
+        o.precision = precision
         self.n = len(rowptr) - 1
         self.h = capi.amgdd_setup(rowptr, col, val, part, nsub, padding, o, stream)
         self.stats = capi.amgdd_get_stats(self.h)

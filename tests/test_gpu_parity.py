@@ -199,3 +199,30 @@ def test_solve_twice_and_new_buffers_recapture():
     for xo, it in outs[1:]:
         assert it == outs[0][1] and np.array_equal(xo, outs[0][0])
     s.close()
+
+
+@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d", "ragged2d"])
+def test_mixed_precision_fac_and_solve_bit_exact(case):
+    """FP32 AlgFAC inside FP64 refinement: GPU states, iterates and iteration
+    count equal the oracle's mixed-precision path bit for bit."""
+    rp, ci, v, part, nsub, pad, b = _case(case)
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, precision=1)
+    rl = o.restrict_all(b)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    capi.amgdd_fac(s.h, _dev(np.concatenate(rl)), x)
+    for p in range(s.nsub):
+        uo, fo = o.algfac32(p, rl, 2)
+        for l in range(s.nlev):
+            g, k = capi.amgdd_get_maps(s.h, p, l)
+            ug, fg = capi.amgdd_get_fac_state(s.h, p, l, len(g))
+            assert np.array_equal(ug, uo[l][g]), (p, l)
+            assert np.array_equal(fg[k < 2], fo[l][g[k < 2]]), (p, l)
+    assert np.array_equal(_host(x), o.amgdd_iteration32(b, np.zeros(s.n), 2))
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x, tol=1e-8, max_iter=100)
+    xo, ho = o.amgdd_solve(b, 2, tol=1e-8, maxit=100, mixed=True)
+    assert info["iterations"] == len(ho) - 1
+    assert np.array_equal(_host(x), xo)
+    assert np.allclose(info["history"], ho, rtol=1e-12, atol=0)
+    s.close()

@@ -127,3 +127,33 @@ def test_amgdd_history_definition():
     x0 = np.random.default_rng(0).uniform(-1, 1, 1024)
     x, h = o.amgdd_solve(np.zeros(1024), 2, x0=x0, tol=1e-6)
     assert h[0] == 1.0 and h[-1] <= 1e-6
+
+
+@pytest.mark.parametrize("kind", ["2d", "3d"])
+def test_fp32_algfac_tracks_fp64_algfac(kind):
+    """The FP32 cycle is the FP64 one up to single-precision rounding."""
+    if kind == "2d":
+        o, A, b = _problem2d(40, 36, (10, 9), 1)
+    else:
+        o, A, b = _problem3d(16, 8, 2)
+    rl = o.restrict_all(b)
+    for p in range(o.nsub):
+        u64, f64 = o.algfac(p, rl, 2)
+        u32, f32 = o.algfac32(p, rl, 2)
+        for l in range(o.nlev):
+            g, k = o.comp_map(p, l)
+            su = abs(u64[l][g]).max()
+            assert abs(u32[l][g] - u64[l][g]).max() <= 2e-5 * su, (p, l)
+            # the FP32 result really is a different (rounded) computation
+        assert not np.array_equal(u32[0], u64[0])
+
+
+def test_mixed_precision_refinement_converges_to_fp64_solution():
+    o, A, b = _problem2d(24, 24, (8, 8), 1, seed=3)
+    xd = np.linalg.solve(A.toarray(), b)
+    xm, hm = o.amgdd_solve(b, 2, tol=1e-11, mixed=True)
+    x64, h64 = o.amgdd_solve(b, 2, tol=1e-11)
+    assert np.linalg.norm(xm - xd) <= 1e-9 * np.linalg.norm(xd)
+    assert abs(len(hm) - len(h64)) <= 2
+    # early iterations: the FP32 correction is as good as the FP64 one
+    assert np.allclose(hm[:4], h64[:4], rtol=1e-4)

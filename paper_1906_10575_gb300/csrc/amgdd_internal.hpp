@@ -87,15 +87,21 @@ struct GlobalLevelDev {
     Sell R;                       // natural row order (l < L)
 };
 
-// One SELL family of the composite-grid layout (see FacViewDev).
+// One SELL family of the composite-grid layout (see FacViewDev). Columns are
+// stored as 16-bit or 32-bit local indices and values as FP64 or FP32, chosen
+// before packing (only one of each pair is filled).
 struct FacView {
     std::vector<int64_t> soff;            // per slice, plus a sentinel per grid-level
     std::vector<uint16_t> rlen;           // per row (row0 + local row)
-    std::vector<int32_t> col;             // local column indices
-    std::vector<double> val;
+    std::vector<uint16_t> col16;
+    std::vector<int32_t> col32;
+    std::vector<double> val64;
+    std::vector<float> val32;
+    bool c16 = true, v32 = false;
     int64_t entries = 0;                  // stored (non-padding) entries
+    size_t size() const { return c16 ? col16.size() : col32.size(); }
+    int32_t col(size_t i) const { return c16 ? (int32_t)col16[i] : col32[i]; }
 };
-
 struct FacLayout {
     int nlev = 0, nsub = 0;
     std::vector<FacLevelDesc> desc;       // [p * nlev + l]
@@ -115,7 +121,7 @@ struct FacLayout {
     std::vector<int64_t> lvA, lvAt, lvAFc, lvP, lvR;
 };
 
-void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads);
+void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads, bool fp32);
 void build_global_dev(const Hierarchy &H, std::vector<GlobalLevelDev> &G);
 
 // Range checks of every index the kernels will dereference; empty if valid.

@@ -347,11 +347,11 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             cudaStream_t st_ = (cudaStream_t)stream;
             h->last_stream = st_;
             FacLayout F;
-            build_fac_layout(h->H, h->C, F, nth);
+            build_fac_layout(h->H, h->C, F, nth, h->opt.precision == 1);
             S.fac_fma = 0;
             for (int p = 0; p < nsub; ++p)
                 S.fac_fma += F.work1[p] + (int64_t)(h->opt.n_fac - 1) * F.work[p];
-            S.fac_entry_bytes = (h->opt.precision == 1 ? 4 : 8) + (F.max_bar < 65536 ? 2 : 4);
+            S.fac_entry_bytes = (h->opt.precision == 1 ? 4 : 8) + (F.A.c16 ? 2 : 4);
             // stored entries of the local operators (padding excluded)
             for (int l = 0; l < nlev; ++l) {
                 S.comp_nnz_A[l] = F.lvA[l];
@@ -435,7 +435,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             }
             if ((e = upload(h, F.owned, &own, st_)) != cudaSuccess) return bail(e, "upload owned");
             if ((e = upload(h, F.owned0, &o0, st_)) != cudaSuccess) return bail(e, "upload owned0");
-            P.col16 = F.max_bar < 65536 ? 1 : 0;
+            P.col16 = F.A.c16 ? 1 : 0;
             P.schedule = h->opt.schedule >= 1 && h->opt.schedule <= 9 ? h->opt.schedule : 8;
             FacView *views[5] = {&F.A, &F.At, &F.AFc, &F.P, &F.R};
             FacViewDev *dviews[5] = {&P.A, &P.At, &P.AFc, &P.P, &P.R};
@@ -443,30 +443,25 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
                 FacView &V = *views[v];
                 int64_t *so;
                 uint16_t *rl;
-                const void *va;
                 if ((e = upload(h, V.soff, &so, st_)) != cudaSuccess) return bail(e, "upload view slices");
                 if ((e = upload(h, V.rlen, &rl, st_)) != cudaSuccess) return bail(e, "upload view rows");
-                if (fp32) {
-                    std::vector<float> vf(V.val.begin(), V.val.end());   // round to nearest FP32
-                    float *vd;
-                    if ((e = upload(h, vf, &vd, st_)) != cudaSuccess) return bail(e, "upload view values");
-                    if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload view values");
-                    va = vd;
+                const void *va, *co;
+                if (V.v32) {
+                    float *d;
+                    if ((e = upload(h, V.val32, &d, st_)) != cudaSuccess) return bail(e, "upload view values");
+                    va = d;
                 } else {
-                    double *vd;
-                    if ((e = upload(h, V.val, &vd, st_)) != cudaSuccess) return bail(e, "upload view values");
-                    va = vd;
+                    double *d;
+                    if ((e = upload(h, V.val64, &d, st_)) != cudaSuccess) return bail(e, "upload view values");
+                    va = d;
                 }
-                const void *co;
-                if (P.col16) {
-                    std::vector<uint16_t> c16(V.col.begin(), V.col.end());
+                if (V.c16) {
                     uint16_t *c;
-                    if ((e = upload(h, c16, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
-                    if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload view columns");
+                    if ((e = upload(h, V.col16, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
                     co = c;
                 } else {
                     int32_t *c;
-                    if ((e = upload(h, V.col, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
+                    if ((e = upload(h, V.col32, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
                     co = c;
                 }
                 if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload views");
@@ -475,36 +470,6 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
                 dviews[v]->col = co;
                 dviews[v]->val = va;
                 V = FacView();
-            }
-            // one bin per SM; grids by decreasing work into the lightest bin
-            {
-                int dev = 0, nsm = 1;
-                if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "device query");
-                if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-                    return bail(e, "device query");
-                const int nb = std::max(1, nsm);
-                std::vector<std::vector<int32_t>> bins((size_t)nb);
-                std::vector<int64_t> load((size_t)nb, 0);
-                for (int32_t g : F.order) {  // F.order: decreasing work
-                    int best = 0;
-                    for (int b = 1; b < nb; ++b)
-                        if (load[b] < load[best]) best = b;
-                    bins[best].push_back(g);
-                    load[best] += F.work[g] > 0 ? F.work[g] : 1;
-                }
-                std::vector<int32_t> off(1, 0), grid;
-                for (auto &bv : bins) {
-                    grid.insert(grid.end(), bv.begin(), bv.end());
-                    off.push_back((int32_t)grid.size());
-                }
-                int32_t *doff, *dgrid, *dctr;
-                if ((e = upload(h, off, &doff, st_)) != cudaSuccess) return bail(e, "upload bins");
-                if ((e = upload(h, grid, &dgrid, st_)) != cudaSuccess) return bail(e, "upload bins");
-                if ((e = alloc(h, (size_t)nb, &dctr)) != cudaSuccess) return bail(e, "alloc bin counters");
-                P.nbins = nb;
-                P.bin_off = doff;
-                P.bin_grid = dgrid;
-                P.ctr = dctr;
             }
             P.desc = dd;
             P.order = ord;

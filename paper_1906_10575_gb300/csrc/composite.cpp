@@ -281,19 +281,21 @@ void emit_view(RowList &rl, int32_t first_row, int32_t rows_total_level, FacView
     for (int32_t s = 0; s * 32 < n; ++s) {
         int64_t width = 0;
         for (int32_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) width = std::max(width, rl.ptr[r + 1] - rl.ptr[r]);
-        const int64_t base = (int64_t)V.col.size();
+        const int64_t base = (int64_t)V.size();
+        const size_t end = (size_t)(base + 32 * width);
         V.soff.push_back(base);
-        V.col.resize((size_t)(base + 32 * width), 0);
-        V.val.resize((size_t)(base + 32 * width), 0.0);
+        if (V.c16) V.col16.resize(end, 0); else V.col32.resize(end, 0);
+        if (V.v32) V.val32.resize(end, 0.0f); else V.val64.resize(end, 0.0);
         for (int32_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) {
             const int lane = r - s * 32;
             for (int64_t k = rl.ptr[r]; k < rl.ptr[r + 1]; ++k) {
-                V.col[(size_t)(base + 32 * (k - rl.ptr[r]) + lane)] = rl.col[k];
-                V.val[(size_t)(base + 32 * (k - rl.ptr[r]) + lane)] = rl.val[k];
+                const size_t o = (size_t)(base + 32 * (k - rl.ptr[r]) + lane);
+                if (V.c16) V.col16[o] = (uint16_t)rl.col[k]; else V.col32[o] = rl.col[k];
+                if (V.v32) V.val32[o] = (float)rl.val[k]; else V.val64[o] = rl.val[k];
             }
         }
     }
-    V.soff.push_back((int64_t)V.col.size());
+    V.soff.push_back((int64_t)V.size());
     for (int32_t r = 0; r < rows_total_level; ++r) {
         const int32_t v = r - first_row;
         V.rlen.push_back(v >= 0 && v < n ? (uint16_t)(rl.ptr[v + 1] - rl.ptr[v]) : (uint16_t)0);
@@ -304,7 +306,7 @@ void emit_view(RowList &rl, int32_t first_row, int32_t rows_total_level, FacView
 
 }  // namespace
 
-void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads)
+void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads, bool fp32)
 {
     const int L = H.L();
     const int nlev = L + 1;
@@ -312,15 +314,37 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
     F.nlev = nlev;
     F.nsub = nsub;
     F.desc.assign((size_t)nsub * nlev, FacLevelDesc{});
-    std::vector<GridBuild> grids((size_t)nsub);
+    // column width and value type are fixed before packing
+    int64_t maxbar = 0;
+    for (const CompLevel &cl : C.g) maxbar = std::max<int64_t>(maxbar, (int64_t)(cl.real.size() + cl.ghost.size()));
+    for (FacView *V : {&F.A, &F.At, &F.AFc, &F.P, &F.R}) {
+        V->c16 = maxbar < 65536;
+        V->v32 = fp32;
+    }
+    // grids are built in chunks (in parallel) and packed (in order) before
+    // the next chunk, so only one chunk's row lists exist at a time
+    const int chunk = std::max(64, 4 * std::max(nthreads, 1));
+    std::vector<GridBuild> grids((size_t)std::min(chunk, std::max(nsub, 1)));
     int32_t nmax = 0;
     for (const auto &lv : H.lv) nmax = std::max(nmax, lv.A.rows);
     const int nt = std::max(nthreads, 1);
     std::vector<std::vector<int32_t>> g2l_s((size_t)nt), g2l_n((size_t)nt), g2l_p((size_t)nt);
     std::vector<std::vector<uint8_t>> realf((size_t)nt), cflag((size_t)nt);
 
-    parallel_for(nsub, nthreads, [&](int p, int t) {
-        GridBuild &G = grids[p];
+    F.gmap.clear();
+    F.owned.clear();
+    F.owned0.assign((size_t)nsub + 1, 0);
+    F.work.assign((size_t)nsub, 0);
+    F.work1.assign((size_t)nsub, 0);
+    F.lvA.assign(nlev, 0); F.lvAt.assign(nlev, 0); F.lvAFc.assign(nlev, 0);
+    F.lvP.assign(nlev, 0); F.lvR.assign(nlev, 0);
+    int64_t row0 = 0;
+    for (int p0 = 0; p0 < nsub; p0 += chunk) {
+    const int pn = std::min(chunk, nsub - p0);
+    parallel_for(pn, nthreads, [&](int pi, int t) {
+        const int p = p0 + pi;
+        GridBuild &G = grids[pi];
+        G = GridBuild();
         G.dev.resize(nlev);
         G.nC.assign(nlev, 0);
         G.nReal.assign(nlev, 0);
@@ -450,16 +474,9 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
         G.work += nL * nL;
     });
 
-    F.gmap.clear();
-    F.owned.clear();
-    F.owned0.assign((size_t)nsub + 1, 0);
-    F.work.assign((size_t)nsub, 0);
-    F.work1.assign((size_t)nsub, 0);
-    F.lvA.assign(nlev, 0); F.lvAt.assign(nlev, 0); F.lvAFc.assign(nlev, 0);
-    F.lvP.assign(nlev, 0); F.lvR.assign(nlev, 0);
-    int64_t row0 = 0;
-    for (int p = 0; p < nsub; ++p) {
-        GridBuild &G = grids[p];
+    for (int pi = 0; pi < pn; ++pi) {
+        const int p = p0 + pi;
+        GridBuild &G = grids[pi];
         for (int l = 0; l <= L; ++l) {
             FacLevelDesc &d = F.desc[(size_t)p * nlev + l];
             const int32_t nbar = (int32_t)G.dev[l].size();
@@ -497,6 +514,7 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
         F.work1[p] = G.work1;
         G = GridBuild();
     }
+    }
     F.rows_total = row0;
     F.order.resize((size_t)nsub);
     std::iota(F.order.begin(), F.order.end(), 0);
@@ -512,14 +530,15 @@ namespace {
 
 // Checks one SELL block: slices cover exactly `rows` rows, every row length
 // fits its slice width, and every stored column lies in [0, ncols).
-std::string check_sell(const std::vector<int64_t> &soff, int64_t s0, const std::vector<uint16_t> &rlen, int64_t r0,
-                       int64_t rows, const std::vector<int32_t> &col, int64_t ncols, const char *what)
+template <class ColAt>
+std::string check_sell_g(const std::vector<int64_t> &soff, int64_t s0, const std::vector<uint16_t> &rlen, int64_t r0,
+                         int64_t rows, size_t ncol_entries, ColAt colat, int64_t ncols, const char *what)
 {
     const int64_t nsl = (rows + 31) / 32;
     if (s0 + nsl >= (int64_t)soff.size() + (rows == 0 ? 1 : 0)) return std::string(what) + ": slice table too short";
     for (int64_t q = 0; q < nsl; ++q) {
         const int64_t a = soff[s0 + q], b = soff[s0 + q + 1];
-        if (a < 0 || b < a || b > (int64_t)col.size() || (b - a) % 32) return std::string(what) + ": bad slice offsets";
+        if (a < 0 || b < a || b > (int64_t)ncol_entries || (b - a) % 32) return std::string(what) + ": bad slice offsets";
         const int64_t width = (b - a) / 32;
         for (int lane = 0; lane < 32; ++lane) {
             const int64_t r = q * 32 + lane;
@@ -528,12 +547,24 @@ std::string check_sell(const std::vector<int64_t> &soff, int64_t s0, const std::
             const int64_t len = rlen[r0 + r];
             if (len > width) return std::string(what) + ": row longer than its slice";
             for (int64_t k = 0; k < len; ++k) {
-                const int32_t c = col[a + 32 * k + lane];
+                const int32_t c = colat((size_t)(a + 32 * k + lane));
                 if (c < 0 || c >= ncols) return std::string(what) + ": column out of range";
             }
         }
     }
     return "";
+}
+
+std::string check_view(const FacView &V, int64_t s0, int64_t r0, int64_t rows, int64_t ncols, const char *what)
+{
+    if ((V.v32 ? V.val32.size() : V.val64.size()) != V.size()) return std::string(what) + ": value array size";
+    return check_sell_g(V.soff, s0, V.rlen, r0, rows, V.size(), [&](size_t i) { return V.col(i); }, ncols, what);
+}
+
+std::string check_sell(const std::vector<int64_t> &soff, int64_t s0, const std::vector<uint16_t> &rlen, int64_t r0,
+                       int64_t rows, const std::vector<int32_t> &col, int64_t ncols, const char *what)
+{
+    return check_sell_g(soff, s0, rlen, r0, rows, col.size(), [&](size_t i) { return col[i]; }, ncols, what);
 }
 
 }  // namespace
@@ -569,15 +600,11 @@ std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDe
             }
             const int64_t nup = l < L ? F.desc[(size_t)p * F.nlev + l + 1].nBar : 0;
             const int64_t ndn = l > 0 ? F.desc[(size_t)p * F.nlev + l - 1].nBar : 0;
-            if (!(e = check_sell(F.A.soff, d.sA, F.A.rlen, d.row0, d.nReal, F.A.col, d.nBar, "local A")).empty()) return e;
-            if (!(e = check_sell(F.At.soff, d.sAt, F.At.rlen, d.row0, d.nBar, F.At.col, d.nReal, "local At")).empty()) return e;
-            if (!(e = check_sell(F.AFc.soff, d.sAFc, F.AFc.rlen, d.row0 + d.nC, d.nReal - d.nC, F.AFc.col, d.nC,
-                                 "local AFc")).empty())
-                return e;
-            if (!(e = check_sell(F.P.soff, d.sP, F.P.rlen, d.row0, l < L ? d.nBar : 0, F.P.col, nup, "local P")).empty())
-                return e;
-            if (!(e = check_sell(F.R.soff, d.sR, F.R.rlen, d.row0, l > 0 ? d.nBar : 0, F.R.col, ndn, "local R")).empty())
-                return e;
+            if (!(e = check_view(F.A, d.sA, d.row0, d.nReal, d.nBar, "local A")).empty()) return e;
+            if (!(e = check_view(F.At, d.sAt, d.row0, d.nBar, d.nReal, "local At")).empty()) return e;
+            if (!(e = check_view(F.AFc, d.sAFc, d.row0 + d.nC, d.nReal - d.nC, d.nC, "local AFc")).empty()) return e;
+            if (!(e = check_view(F.P, d.sP, d.row0, l < L ? d.nBar : 0, nup, "local P")).empty()) return e;
+            if (!(e = check_view(F.R, d.sR, d.row0, l > 0 ? d.nBar : 0, ndn, "local R")).empty()) return e;
             if (l == L && d.nBar != H.lv[L].A.rows) return "coarsest composite level is not whole";
             if (l == L && d.nReal != d.nBar) return "coarsest composite level has ghosts";
         }

@@ -261,6 +261,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-multi", action="store_true", help="skip the four-right-hand-side measurement")
     ap.add_argument("--schedule", type=int, default=0, help="FAC kernel variant (0 = library default)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid edge (default 128, the benchmark workload; smaller edges "
@@ -400,6 +401,46 @@ def main():
                  "dtype": "f32 AlgFAC / f64 refinement"}
         sm.close()
 
+    # four right-hand sides of the same matrix at once (FP64): every operator
+    # entry feeds four fma chains
+    multi = None
+    if not args.no_multi:
+        sq = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                    stream=stream)
+        Bm = torch.from_numpy(np.ascontiguousarray(np.stack([I.uniform_rhs(sq.n, j) for j in range(4)], 1))).cuda()
+        Xm = torch.zeros_like(Bm)
+        with torch.cuda.stream(stream):
+            def tmm(k):
+                ts, inf = [], None
+                for _ in range(k):
+                    Xm.zero_()
+                    torch.cuda.synchronize()
+                    a0 = torch.cuda.Event(enable_timing=True)
+                    a1 = torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    inf = sq.solve_multi(Bm, Xm, tol=TOL, max_iter=200, stream=stream)
+                    a1.record(stream)
+                    a1.synchronize()
+                    ts.append(a0.elapsed_time(a1))
+                return ts, inf
+            tmm(args.warmup)
+            t_mm, i_mm = tmm(args.steps)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            capi.amgdd_iterate_multi(sq.h, Bm, Xm, stream)
+            a0.record(stream)
+            for _ in range(nf):
+                capi.amgdd_iterate_multi(sq.h, Bm, Xm, stream)
+            a1.record(stream)
+            a1.synchronize()
+            it_mm = a0.elapsed_time(a1) / nf
+        ms_mm = max_over_ranks([statistics.median(t_mm)], dist)[0]
+        multi = {"nrhs": 4, "ms_all_columns": round(ms_mm, 3), "ms_per_column": round(ms_mm / 4, 3),
+                 "iterations": i_mm["iterations"], "final_relres_max": i_mm["final_relres"],
+                 "ms_per_iteration": round(it_mm, 3),
+                 "dtype": "f64"}
+        sq.close()
+
     ms_dd = statistics.median(t_dd)
     ms_v = statistics.median(t_v)
     ms_e2e = statistics.median(t_e2e)
@@ -451,6 +492,7 @@ def main():
                 "d2h_bytes_per_step": 8 * s.n},
         "clocks": clocks,
         "mixed_precision": mixed,
+        "multi_rhs": multi,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, it_dd)

@@ -215,6 +215,27 @@ amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream
 amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double tol,
                               int32_t max_iter, void *stream, amgdd_solve_info *info);
 
+/* ---- several right-hand sides at once --------------------------------------
+ * Right-hand sides of the same matrix solved together (nrhs = 2 or 4): B and X
+ * are DEVICE arrays of n x nrhs doubles stored row by row (X[i * nrhs + j] is
+ * unknown i of column j, i.e. a contiguous torch tensor of shape (n, nrhs)).
+ * Every operator entry is loaded once per use and feeds nrhs independent fma
+ * chains; column j follows exactly the single-column arithmetic of
+ * amgdd_iterate / amgdd_solve, so its iterates are the ones that a solve of
+ * column j alone would produce after the same number of iterations. The first
+ * call with a given nrhs allocates that width's device work space. */
+
+/* One AMG-DD iteration (Algorithm 2) for all columns. */
+amgdd_status amgdd_iterate_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, void *stream);
+
+/* AMG-DD solver for all columns: iterates until every column satisfies
+ * ||b_j - A x_j|| / ||b_j|| <= tol (or max_iter). info->history (HOST, may be
+ * NULL) receives nrhs * (max_iter + 1) doubles, column j's history at
+ * history[j * (max_iter + 1) + k]; info->final_relres is the largest final
+ * relative residual over the columns. */
+amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, double tol,
+                               int32_t max_iter, void *stream, amgdd_solve_info *info);
+
 /* ---- residual without any device allocation ------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * cannot call cudaMalloc at the moment they need a residual, for example code

@@ -61,7 +61,7 @@ EXPORTS = [
     "amgdd_last_error", "amgdd_get_stats", "amgdd_get_maps", "amgdd_get_operator", "amgdd_get_cf",
     "amgdd_get_coarse_inverse", "amgdd_residual", "amgdd_restrict", "amgdd_fac",
     "amgdd_get_fac_state", "amgdd_iterate", "amgdd_solve", "amg_vcycle", "amg_vcycle_solve",
-    "amgdd_residual_csr_noalloc",
+    "amgdd_residual_csr_noalloc", "amgdd_iterate_multi", "amgdd_solve_multi",
 ]
 
 _lib = None
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
         "amg_vcycle": [vp, vp, vp, vp],
         "amg_vcycle_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
         "amgdd_residual_csr_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
+        "amgdd_iterate_multi": [vp, vp, vp, i32, vp],
+        "amgdd_solve_multi": [vp, vp, vp, i32, f64, i32, vp, C.POINTER(amgdd_solve_info)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -276,3 +278,24 @@ def amgdd_residual_csr_noalloc(n, rowptr, col, val, b, x, r, nrm2, stream=None):
     (all arguments are device tensors the caller owns)."""
     _check(load().amgdd_residual_csr_noalloc(int(n), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b),
                                               _ptr(x), _ptr(r), _ptr(nrm2), _stream(stream)))
+
+
+def amgdd_iterate_multi(h, B, X, stream=None):
+    """One AMG-DD iteration for every column of B / X (device, shape (n, nrhs))."""
+    _check(load().amgdd_iterate_multi(h, _ptr(B), _ptr(X), int(B.shape[1]), _stream(stream)), h)
+
+
+def amgdd_solve_multi(h, B, X, tol=1e-8, max_iter=200, stream=None, raise_on_noconv=True):
+    """AMG-DD for all columns of B / X (device, shape (n, nrhs), nrhs = 2 or 4)."""
+    nrhs = int(B.shape[1])
+    hist = np.zeros(nrhs * (max_iter + 1), np.float64)
+    info = amgdd_solve_info()
+    info.history = hist.ctypes.data_as(C.POINTER(C.c_double))
+    st = load().amgdd_solve_multi(h, _ptr(B), _ptr(X), nrhs, float(tol), int(max_iter), _stream(stream),
+                                  C.byref(info))
+    if st != 0 and not (st == 6 and not raise_on_noconv):
+        _check(st, h)
+    k = info.iterations
+    return dict(iterations=k, converged=bool(info.converged), final_relres=info.final_relres,
+                history=hist.reshape(nrhs, max_iter + 1)[:, :k + 1].copy(), seconds=info.seconds,
+                kernel_launches=info.kernel_launches)

@@ -68,6 +68,15 @@ struct amgdd_handle_s {
         int64_t launches = 0;
     } graph[2];
     cudaStream_t cap_stream = nullptr;
+    // work space of the several-right-hand-side path, per width (2 or 4)
+    struct Multi {
+        int R = 0;
+        void *ws[6] = {};
+        double *r_all = nullptr, *partial = nullptr, *scal = nullptr, *h_scal = nullptr;
+        Graph graph;
+    } multi[2];
+    int64_t fac_rows = 0;
+    FacParams fac_base{};
 };
 
 namespace {
@@ -260,6 +269,10 @@ void amgdd_destroy(amgdd_handle h)
         cudaStreamSynchronize(h->last_stream);
         for (auto &g : h->graph)
             if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (auto &m : h->multi) {
+            if (m.graph.exec) cudaGraphExecDestroy(m.graph.exec);
+            if (m.h_scal) cudaFreeHost(m.h_scal);
+        }
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         for (void *p : h->allocs) cudaFree(p);
         if (h->h_scal) cudaFreeHost(h->h_scal);
@@ -495,6 +508,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "setup upload");
             h->desc = F.desc;
             h->dev2map = F.dev2map;
+            h->fac_rows = F.rows_total;
             h->on_device = true;
         }
     done:
@@ -814,6 +828,149 @@ static amgdd_status solve_loop(amgdd_handle h, const double *b, double *x, doubl
         info->kernel_launches = h->launches - l0;
     }
     if (!(rel <= tol)) return fail(h, AMGDD_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+    return AMGDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Several right-hand sides.
+
+static amgdd_status multi_space(amgdd_handle h, int R, amgdd_handle_s::Multi **out)
+{
+    auto &m = h->multi[R == 2 ? 0 : 1];
+    if (m.R != R) {
+        const size_t elt = h->fac.fp32 ? sizeof(float) : sizeof(double);
+        for (int k = 0; k < 6; ++k) {
+            void *p = nullptr;
+            CK(cudaMalloc(&p, std::max<size_t>(1, (size_t)h->fac_rows * R * elt)), "alloc multi work space");
+            h->allocs.push_back(p);
+            h->dev_bytes += (int64_t)h->fac_rows * R * (int64_t)elt;
+            m.ws[k] = p;
+        }
+        CK(alloc(h, (size_t)h->level_off.back() * R, &m.r_all), "alloc multi residual");
+        CK(alloc(h, (size_t)h->nred * R, &m.partial), "alloc multi partial sums");
+        CK(alloc(h, (size_t)2 * R, &m.scal), "alloc multi scalars");
+        CK(cudaMallocHost((void **)&m.h_scal, sizeof(double) * 2 * R), "alloc multi pinned");
+        m.R = R;
+    }
+    *out = &m;
+    return AMGDD_OK;
+}
+
+static amgdd_status iterate_multi(amgdd_handle h, amgdd_handle_s::Multi &m, const double *B, double *X, bool fresh_residual,
+                                  cudaStream_t st)
+{
+    const int R = m.R;
+    if (fresh_residual) {
+        CK(launch_residual_multi(h->lev[0].A, B, X, m.r_all, m.partial, h->nred, m.scal, R, st), "residual kernel");
+        h->launches += 2;
+    }
+    const int nlev = (int)h->lev.size();
+    for (int l = 0; l + 1 < nlev; ++l) {
+        CK(launch_spmv_multi(h->lev[l].R, m.r_all + h->level_off[l] * R, m.r_all + h->level_off[l + 1] * R, R, st),
+           "restriction kernel");
+        h->launches += 1;
+    }
+    FacParams P = h->fac;
+    P.u = m.ws[0]; P.f = m.ws[1]; P.t = m.ws[2]; P.s = m.ws[3]; P.w = m.ws[4]; P.d = m.ws[5];
+    P.r_all = m.r_all;
+    P.x = X;
+    CK(launch_fac_multi(P, P.nsub, R, st), "FAC kernel");
+    h->launches += 1;
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_iterate_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!B || !X || (nrhs != 2 && nrhs != 4)) return fail(h, AMGDD_ERR_INVALID_ARG, "nrhs must be 2 or 4");
+    amgdd_handle_s::Multi *m;
+    if ((s = multi_space(h, nrhs, &m)) != AMGDD_OK) return s;
+    h->last_stream = (cudaStream_t)stream;
+    return iterate_multi(h, *m, B, X, true, (cudaStream_t)stream);
+}
+
+amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, double tol, int32_t max_iter,
+                               void *stream, amgdd_solve_info *info)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!B || !X || (nrhs != 2 && nrhs != 4) || max_iter < 0 || !(tol >= 0.0))
+        return fail(h, AMGDD_ERR_INVALID_ARG, "bad multi-column solve arguments");
+    amgdd_handle_s::Multi *mp;
+    if ((s = multi_space(h, nrhs, &mp)) != AMGDD_OK) return s;
+    auto &m = *mp;
+    const int R = nrhs;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t l0 = h->launches;
+    // one iteration = restriction + FAC + residual of the new iterate + the
+    // copy of the squared column norms, captured once per (B, X)
+    if (!(m.graph.exec && m.graph.b == B && m.graph.x == X)) {
+        if (m.graph.exec) {
+            cudaGraphExecDestroy(m.graph.exec);
+            m.graph.exec = nullptr;
+        }
+        if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+        const int64_t c0 = h->launches;
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        amgdd_status cs = iterate_multi(h, m, B, X, false, h->cap_stream);
+        if (cs == AMGDD_OK) {
+            cudaError_t e = launch_residual_multi(h->lev[0].A, B, X, m.r_all, m.partial, h->nred, m.scal, R,
+                                                  h->cap_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(m.h_scal, m.scal, sizeof(double) * R, cudaMemcpyDeviceToHost, h->cap_stream);
+            h->launches += 2;
+            if (e != cudaSuccess) cs = cuda_fail(h, e, "capture residual");
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (cs != AMGDD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return cs;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+        e = cudaGraphInstantiate(&m.graph.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+        m.graph.b = B;
+        m.graph.x = X;
+        m.graph.launches = h->launches - c0;
+        h->launches = c0;
+    }
+    CK(launch_sumsq_multi(B, h->lev[0].n, m.partial, h->nred, m.scal + R, R, st), "norm kernel");
+    CK(launch_residual_multi(h->lev[0].A, B, X, m.r_all, m.partial, h->nred, m.scal, R, st), "residual kernel");
+    h->launches += 4;
+    CK(cudaMemcpyAsync(m.h_scal, m.scal, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, st), "norm copy");
+    CK(cudaStreamSynchronize(st), "residual");
+    double ref[4], rel[4];
+    for (int j = 0; j < R; ++j) ref[j] = std::sqrt(m.h_scal[R + j]);
+    int32_t k = 0;
+    double worst = 0.0;
+    for (;;) {
+        worst = 0.0;
+        for (int j = 0; j < R; ++j) {
+            const double nr = std::sqrt(m.h_scal[j]);
+            if (k == 0 && ref[j] == 0.0) ref[j] = nr;
+            rel[j] = ref[j] > 0.0 ? nr / ref[j] : 0.0;
+            if (info && info->history) info->history[(size_t)j * (max_iter + 1) + k] = rel[j];
+            worst = std::max(worst, rel[j]);
+        }
+        if (worst <= tol || k >= max_iter) break;
+        CK(cudaGraphLaunch(m.graph.exec, st), "graph launch");
+        CK(cudaStreamSynchronize(st), "iteration");
+        h->launches += m.graph.launches;
+        ++k;
+    }
+    if (info) {
+        info->iterations = k;
+        info->converged = worst <= tol;
+        info->final_relres = worst;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->kernel_launches = h->launches - l0;
+    }
+    if (!(worst <= tol)) return fail(h, AMGDD_ERR_NO_CONVERGENCE, "max_iter reached before tol");
     return AMGDD_OK;
 }
 

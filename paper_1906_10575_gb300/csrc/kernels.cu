@@ -8,6 +8,7 @@
 // Built with -fmad=false: only the explicit fma() calls fuse.
 #include <cstdint>
 
+#include "fac_device.cuh"
 #include "kernels.cuh"
 
 namespace amgdd {
@@ -170,20 +171,6 @@ __global__ void k_coarse_solve(const double *__restrict__ ainv, int n, const dou
 // All composite grids, one CTA each: gather f_l = r_l on D_l, n_fac AlgFAC
 // V(1,1)-cycles (Algorithm 4), add u_0 on the owned points into x.
 
-struct Block {
-    int lane, warp, nw, tid, nt;
-};
-
-// Loads of operator entries, which every launch streams once: evict-first
-// (ld.global.cs) when STREAM is set, so they do not push the composite-grid
-// vectors out of L2; read-only path (ld.global.nc) otherwise.
-template <bool STREAM, class X>
-__device__ __forceinline__ X ld_op(const X *p)
-{
-    if constexpr (STREAM) return __ldcs(p);
-    else return __ldg(p);
-}
-
 // Row product of local row `r` of a composite-grid view whose slices start at
 // local row `first`: slice q = (r - first) / 32, lane = (r - first) % 32. T is
 // the arithmetic type of the composite grid (double, or float in the mixed-
@@ -307,32 +294,6 @@ __device__ __forceinline__ double view_dot_async(const FacViewDev &V, int64_t sl
         __syncwarp();
     }
     return s;
-}
-
-// Local rows [r0, r1) of a view whose slices start at local row `first`
-// (r0 >= first), thread-per-row, warp-per-slice.
-template <class Fn>
-__device__ __forceinline__ void for_rows(const Block &B, int first, int r0, int r1, Fn &&fn)
-{
-    if (r1 <= r0) return;
-    const int q0 = (r0 - first) >> 5, q1 = (r1 - first + 31) >> 5;
-    for (int q = q0 + B.warp; q < q1; q += B.nw) {
-        const int r = first + (q << 5) + B.lane;
-        if (r >= r0 && r < r1) fn(r);
-    }
-}
-
-// Warp-uniform traversal of the slices covering local rows [r0, r1) of a view
-// whose slices start at `first`; fn(q, r, active) is called by every lane.
-template <class Fn>
-__device__ __forceinline__ void for_slices(const Block &B, int first, int r0, int r1, Fn &&fn)
-{
-    if (r1 <= r0) return;
-    const int q0 = (r0 - first) >> 5, q1 = (r1 - first + 31) >> 5;
-    for (int q = q0 + B.warp; q < q1; q += B.nw) {
-        const int r = first + (q << 5) + B.lane;
-        fn(q, r, r >= r0 && r < r1);
-    }
 }
 
 // Row product of local row r of a view: direct loads (K == 0) or staged

@@ -81,6 +81,13 @@ cudaError_t launch_relax_apply(const int32_t *rowid, int64_t r0, int64_t r1, con
                                cudaStream_t st);
 cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, double *u, cudaStream_t st);
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st);
+// several right-hand sides (nrhs = 2 or 4), vectors stored row by row
+cudaError_t launch_fac_multi(const FacParams &P, int nsub, int nrhs, cudaStream_t st);
+cudaError_t launch_residual_multi(const SellView &A, const double *b, const double *x, double *r, double *partial,
+                                  int nblocks, double *out, int nrhs, cudaStream_t st);
+cudaError_t launch_sumsq_multi(const double *v, int64_t n, double *partial, int nblocks, double *out, int nrhs,
+                               cudaStream_t st);
+cudaError_t launch_spmv_multi(const SellView &M, const double *x, double *y, int nrhs, cudaStream_t st);
 // resident CTAs per SM of the selected FAC kernel variant
 cudaError_t fac_blocks_per_sm(const FacParams &P, int threads, int *blocks);
 

@@ -49,3 +49,7 @@ class Solver:
 
     def vcycle_solve(self, b, x, tol=1e-8, max_iter=200, stream=None):
         return capi.amg_vcycle_solve(self.h, b, x, tol, max_iter, stream)
+
+    def solve_multi(self, B, X, tol=1e-8, max_iter=200, stream=None):
+        """All columns of B / X (device tensors of shape (n, 2) or (n, 4))."""
+        return capi.amgdd_solve_multi(self.h, B, X, tol, max_iter, stream)

@@ -226,3 +226,37 @@ def test_mixed_precision_fac_and_solve_bit_exact(case):
     assert np.array_equal(_host(x), xo)
     assert np.allclose(info["history"], ho, rtol=1e-12, atol=0)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nrhs", [2, 4])
+@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d"])
+def test_multi_rhs_columns_equal_single_column_solves(case, nrhs, precision):
+    """Columns solved together follow exactly the single-column arithmetic:
+    each column's iterate after k iterations equals the oracle's k
+    iterations on that column alone."""
+    rp, ci, v, part, nsub, pad, _ = _case(case)
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, precision=precision)
+    n = s.n
+    Bh = np.stack([I.uniform_rhs(n, 10 + j) for j in range(nrhs)], axis=1)
+    B = torch.from_numpy(np.ascontiguousarray(Bh)).cuda()
+    X = torch.zeros((n, nrhs), dtype=torch.float64, device="cuda")
+    capi.amgdd_iterate_multi(s.h, B, X)
+    Xh = _host(X)
+    step = o.amgdd_iteration32 if precision else (lambda b, x, nf: o.amgdd_iteration(b, x, nf))
+    for j in range(nrhs):
+        assert np.array_equal(Xh[:, j], step(Bh[:, j], np.zeros(n), 2)), j
+    X.zero_()
+    info = s.solve_multi(B, X, tol=1e-8, max_iter=100)
+    Xh = _host(X)
+    k = info["iterations"]
+    for j in range(nrhs):
+        xo = np.zeros(n)
+        for _ in range(k):
+            xo = step(Bh[:, j], xo, 2)
+        assert np.array_equal(Xh[:, j], xo), j
+        _, ho = o.amgdd_solve(Bh[:, j], 2, tol=0.0, maxit=k, mixed=bool(precision))
+        assert np.allclose(info["history"][j], ho, rtol=1e-12, atol=0), j
+    assert info["converged"] and info["history"][:, -1].max() <= 1e-8
+    s.close()

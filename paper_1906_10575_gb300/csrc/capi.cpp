@@ -484,6 +484,37 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
                 dviews[v]->val = va;
                 V = FacView();
             }
+            // one bin per SM; grids by decreasing work into the lightest bin
+            {
+                int dev = 0, nsm = 1;
+                if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "device query");
+                if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                    return bail(e, "device query");
+                const int nb = std::max(1, nsm);
+                std::vector<std::vector<int32_t>> bins((size_t)nb);
+                std::vector<int64_t> load((size_t)nb, 0);
+                for (int32_t g : F.order) {  // F.order: decreasing work
+                    int best = 0;
+                    for (int b = 1; b < nb; ++b)
+                        if (load[b] < load[best]) best = b;
+                    bins[best].push_back(g);
+                    load[best] += F.work[g] > 0 ? F.work[g] : 1;
+                }
+                std::vector<int32_t> off(1, 0), grid;
+                for (auto &bv : bins) {
+                    grid.insert(grid.end(), bv.begin(), bv.end());
+                    off.push_back((int32_t)grid.size());
+                }
+                int32_t *doff, *dgrid, *dctr;
+                if ((e = upload(h, off, &doff, st_)) != cudaSuccess) return bail(e, "upload bins");
+                if ((e = upload(h, grid, &dgrid, st_)) != cudaSuccess) return bail(e, "upload bins");
+                if ((e = alloc(h, (size_t)nb, &dctr)) != cudaSuccess) return bail(e, "alloc bin counters");
+                if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload bins");
+                P.nbins = nb;
+                P.bin_off = doff;
+                P.bin_grid = dgrid;
+                P.ctr = dctr;
+            }
             P.desc = dd;
             P.order = ord;
             P.gmap = gm;

@@ -609,6 +609,7 @@ static cudaError_t launch_fac_ci(const FacParams &P, int nsub, int threads, cuda
 
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st)
 {
+    if (P.nbins < 1 || !P.ctr || !P.bin_off || !P.bin_grid || !P.desc || !P.u) return cudaErrorInvalidValue;
     return P.col16 ? launch_fac_ci<uint16_t>(P, nsub, threads, st, nullptr)
                    : launch_fac_ci<int32_t>(P, nsub, threads, st, nullptr);
 }

@@ -397,6 +397,7 @@ static cudaError_t launch_fac_r_ci(const FacParams &P, int nsub, cudaStream_t st
 
 cudaError_t launch_fac_multi(const FacParams &P, int nsub, int nrhs, cudaStream_t st)
 {
+    if (P.nbins < 1 || !P.ctr || !P.bin_off || !P.bin_grid || !P.desc || !P.u) return cudaErrorInvalidValue;
     switch (nrhs) {
     case 2: return launch_fac_r_ci<2>(P, nsub, st);
     case 4: return launch_fac_r_ci<4>(P, nsub, st);

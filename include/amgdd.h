@@ -80,7 +80,12 @@ typedef struct {
                                rounded to FP32, fp32 fma chains), inside FP64
                                iterative refinement: residual, restriction,
                                coarsest solve and x += u_0 stay FP64 */
-    int32_t reserved[6];
+    int32_t hybrid_level;   /* 0 = none; Lt >= 1 also builds the composite grids of
+                               the hierarchy from level Lt down for hybrid AMG-DD
+                               (Algorithm 3, amg_hybrid_cycle / amg_hybrid_solve);
+                               subdomains on level Lt are inherited from the
+                               partition through the C points (FP64) */
+    int32_t reserved[5];
 } amgdd_options;
 
 /* Statistics of a completed setup. */
@@ -214,6 +219,18 @@ amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream
 /* V-cycle solver on the same hierarchy, same stopping rule as amgdd_solve. */
 amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double tol,
                               int32_t max_iter, void *stream, amgdd_solve_info *info);
+
+/* Hybrid AMG-DD V(1,1)-cycle (Section 3.1, Algorithm 3) in place on x with
+ * right-hand side b: CF l1-Jacobi V-cycle relaxation and restriction on levels
+ * 0 .. Lt-1, then one AMG-DD cycle (Algorithm 2 with AlgFAC, from the current
+ * level-Lt correction) in place of the coarse solve on level Lt, then the
+ * V-cycle's interpolation and relaxation. Lt = opts->hybrid_level (>= 1);
+ * b, x: DEVICE, n doubles. */
+amgdd_status amg_hybrid_cycle(amgdd_handle h, const double *b, double *x, void *stream);
+
+/* Hybrid AMG-DD solver, same stopping rule as amgdd_solve. */
+amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                              void *stream, amgdd_solve_info *info);
 
 /* ---- several right-hand sides at once --------------------------------------
  * Right-hand sides of the same matrix solved together (nrhs = 2 or 4): B and X

@@ -1283,6 +1283,134 @@ void orc_amgdd_iteration32(void *h, void *c, const double *b, double *x, int nfa
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Hybrid AMG-DD (Algorithm 3)                                          */
+/* ------------------------------------------------------------------ */
+
+/* The hierarchy from level lev0 down, sharing the operators of h (a view:
+ * orc_hier_sub_free releases only the view). */
+void *orc_hier_sub(void *h, int lev0)
+{
+    Hier *H = h;
+    Hier *S = xcalloc(1, sizeof(Hier));
+    S->nlev = H->nlev - lev0;
+    for (int l = 0; l < S->nlev; ++l) {
+        S->A[l] = H->A[lev0 + l];
+        S->P[l] = H->P[lev0 + l];
+        S->R[l] = H->R[lev0 + l];
+        S->cf[l] = H->cf[lev0 + l];
+        S->cmap[l] = H->cmap[lev0 + l];
+        S->l1inv[l] = H->l1inv[lev0 + l];
+    }
+    S->ainv = H->ainv;
+    return S;
+}
+
+void orc_hier_sub_free(void *s) { free(s); }
+
+/* Subdomain of every point of level lev0: each C point carries the subdomain
+ * of the fine point it comes from. part_out: n_lev0 entries. */
+void orc_part_on_level(void *h, const int *part, int lev0, int *part_out)
+{
+    Hier *H = h;
+    int n = H->A[0].n;
+    int *cur = xmalloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    memcpy(cur, part, sizeof(int) * (size_t)n);
+    for (int l = 0; l < lev0; ++l) {
+        int nc = H->A[l + 1].n;
+        int *nx = xmalloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+        for (int i = 0; i < H->A[l].n; ++i)
+            if (H->cf[l][i]) nx[H->cmap[l][i]] = cur[i];
+        free(cur);
+        cur = nx;
+    }
+    memcpy(part_out, cur, sizeof(int) * (size_t)H->A[lev0].n);
+    free(cur);
+}
+
+/* One hybrid V(1,1)-cycle (Algorithm 3) in place on (u_0, f_0): V-cycle
+ * relaxation / restriction on levels 0 .. lev0-1, then one AMG-DD cycle on
+ * level lev0 in place of the coarse solve (r = f - A u on that level, its
+ * restrictions through the sub-hierarchy, AlgFAC on every composite grid of
+ * the sub-hierarchy, owned corrections added into u_lev0), then the upsweep.
+ * hs: the sub-hierarchy view from lev0; cs: its composite grids. */
+void orc_hybrid_apply(void *h, void *hs, void *cs, int lev0, int nfac, const double *f0, double *u0)
+{
+    Hier *H = h;
+    Hier *HS = hs;
+    Comp *CS = cs;
+    int L = H->nlev - 1;
+    int64_t off[ORC_MAXLEV + 1];
+    off[0] = 0;
+    for (int l = 0; l <= L; ++l) off[l + 1] = off[l] + H->A[l].n;
+    double *U = xcalloc((size_t)off[L + 1], sizeof(double));
+    double *F = xcalloc((size_t)off[L + 1], sizeof(double));
+    double *W = xcalloc((size_t)H->A[0].n, sizeof(double));
+    double *u[ORC_MAXLEV], *f[ORC_MAXLEV];
+    u[0] = u0;
+    f[0] = (double *)f0;
+    for (int l = 1; l <= L; ++l) { u[l] = U + off[l]; f[l] = F + off[l]; }
+    for (int l = 0; l < lev0; ++l) {
+        const Mat *A = &H->A[l];
+        relax_pass(A, H->l1inv[l], H->cf[l], 1, NULL, A->n, f[l], u[l], NULL, W);
+        relax_pass(A, H->l1inv[l], H->cf[l], 0, NULL, A->n, f[l], u[l], NULL, W);
+        for (int i = 0; i < A->n; ++i) W[i] = f[l][i] - rowdot(A, i, u[l]);
+        for (int I = 0; I < H->R[l].n; ++I) f[l + 1][I] = rowdot(&H->R[l], I, W);
+        for (int I = 0; I < H->A[l + 1].n; ++I) u[l + 1][I] = 0.0;
+    }
+    /* AMG-DD cycle on level lev0 (Algorithm 2 on A_lev0 u = f_lev0) */
+    {
+        int64_t tot = 0;
+        for (int l = 0; l < HS->nlev; ++l) tot += HS->A[l].n;
+        double *rl = xcalloc((size_t)tot, sizeof(double));
+        const Mat *A = &HS->A[0];
+        for (int i = 0; i < A->n; ++i) rl[i] = f[lev0][i] - rowdot(A, i, u[lev0]);
+        orc_restrict_all(HS, rl);
+        FacWork FW;
+        facwork_init(HS, &FW);
+        for (int p = 0; p < CS->nsub; ++p) {
+            algfac(HS, CS, p, rl, nfac, &FW);
+            const CLevel *c0 = &CS->lv[(size_t)p * CS->nlev];
+            for (int q = 0; q < c0->nowned; ++q) {
+                int i = c0->owned[q];
+                u[lev0][i] = u[lev0][i] + FW.u[i];
+            }
+            facwork_clear(HS, CS, p, &FW);
+        }
+        facwork_free(&FW);
+        free(rl);
+    }
+    for (int l = lev0 - 1; l >= 0; --l) {
+        const Mat *A = &H->A[l];
+        for (int i = 0; i < A->n; ++i) u[l][i] = u[l][i] + rowdot(&H->P[l], i, u[l + 1]);
+        relax_pass(A, H->l1inv[l], H->cf[l], 0, NULL, A->n, f[l], u[l], NULL, W);
+        relax_pass(A, H->l1inv[l], H->cf[l], 1, NULL, A->n, f[l], u[l], NULL, W);
+    }
+    free(U); free(F); free(W);
+}
+
+int orc_hybrid_solve(void *h, void *hs, void *cs, int lev0, int nfac, const double *b, double *x, double tol,
+                     int maxit, double *hist)
+{
+    Hier *H = h;
+    int n = H->A[0].n;
+    double *r = xcalloc((size_t)n, sizeof(double));
+    double ref = norm2(b, n);
+    int k = 0;
+    for (;;) {
+        orc_residual(h, b, x, r);
+        double nr = norm2(r, n);
+        if (k == 0 && ref == 0.0) ref = nr;
+        double rel = ref > 0.0 ? nr / ref : 0.0;
+        hist[k] = rel;
+        if (rel <= tol || k >= maxit) break;
+        orc_hybrid_apply(h, hs, cs, lev0, nfac, b, x);
+        ++k;
+    }
+    free(r);
+    return k;
+}
+
 /* AMG-DD solver: iterations of Algorithm 2 until ||b - A x|| / ||b|| <= tol. */
 int orc_amgdd_solve(void *h, void *c, const double *b, double *x, double tol, int maxit, int nfac, int mixed,
                     double *hist)

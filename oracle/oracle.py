@@ -74,6 +74,12 @@ def oracle_lib():
             "orc_amgdd_iteration": (None, [vp, vp, f64p, f64p, C.c_int, i32p, C.c_int, f64p]),
             "orc_amgdd_solve": (C.c_int, [vp, vp, f64p, f64p, C.c_double, C.c_int, C.c_int, C.c_int, f64p]),
             "orc_algfac32": (None, [vp, vp, C.c_int, f64p, C.c_int, f64p, f64p]),
+            "orc_hier_sub": (vp, [vp, C.c_int]),
+            "orc_hier_sub_free": (None, [vp]),
+            "orc_part_on_level": (None, [vp, i32p, C.c_int, i32p]),
+            "orc_hybrid_apply": (None, [vp, vp, vp, C.c_int, C.c_int, f64p, f64p]),
+            "orc_hybrid_solve": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, f64p, f64p, C.c_double, C.c_int,
+                                          f64p]),
             "orc_amgdd_iteration32": (None, [vp, vp, f64p, f64p, C.c_int, f64p]),
         }
         for name, (res, args) in sig.items():
@@ -127,10 +133,15 @@ class Oracle:
                     pad = np.concatenate([pad, np.full(self.nlev - len(pad), pad[-1], np.int32)])
             self.nsub = int(nsub)
             self.padding = pad
+            self.part = part
             self.c = lib.orc_comp_build(self.h, part, self.nsub, pad)
+        self._hyb = {}
 
     def __del__(self):
         try:
+            for hs, cs in getattr(self, "_hyb", {}).values():
+                self.lib.orc_comp_free(cs)
+                self.lib.orc_hier_sub_free(hs)
             if self.c:
                 self.lib.orc_comp_free(self.c)
             if self.h:
@@ -265,3 +276,29 @@ class Oracle:
         rl = np.zeros(int(self.offsets[-1]))
         self.lib.orc_amgdd_iteration32(self.h, self.c, _c64(b), x, int(nfac), rl)
         return x
+
+
+    # ---- hybrid AMG-DD (Algorithm 3) ---------------------------------------
+    def _hybrid(self, lev0):
+        if lev0 not in self._hyb:
+            hs = self.lib.orc_hier_sub(self.h, int(lev0))
+            pl = np.zeros(self.level_n[lev0], np.int32)
+            self.lib.orc_part_on_level(self.h, self.part, int(lev0), pl)
+            cs = self.lib.orc_comp_build(hs, pl, self.nsub,
+                                         np.ascontiguousarray(self.padding[lev0:], np.int32))
+            self._hyb[lev0] = (hs, cs)
+        return self._hyb[lev0]
+
+    def hybrid_apply(self, lev0, f, u, nfac):
+        hs, cs = self._hybrid(lev0)
+        u = _c64(u).copy()
+        self.lib.orc_hybrid_apply(self.h, hs, cs, int(lev0), int(nfac), _c64(f), u)
+        return u
+
+    def hybrid_solve(self, lev0, b, nfac, x0=None, tol=1e-8, maxit=200):
+        hs, cs = self._hybrid(lev0)
+        x = np.zeros(self.n) if x0 is None else _c64(x0).copy()
+        hist = np.zeros(maxit + 1)
+        k = self.lib.orc_hybrid_solve(self.h, hs, cs, int(lev0), int(nfac), _c64(b), x, float(tol),
+                                      int(maxit), hist)
+        return x, hist[:k + 1]

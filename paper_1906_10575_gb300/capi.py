@@ -35,7 +35,7 @@ class amgdd_options(C.Structure):
     _fields_ = [("theta", C.c_double), ("max_coarse", C.c_int32), ("max_levels", C.c_int32),
                 ("n_fac", C.c_int32), ("strict_assumption", C.c_int32), ("host_only", C.c_int32),
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("precision", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("hybrid_level", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class amgdd_setup_stats(C.Structure):
@@ -62,6 +62,7 @@ EXPORTS = [
     "amgdd_get_coarse_inverse", "amgdd_residual", "amgdd_restrict", "amgdd_fac",
     "amgdd_get_fac_state", "amgdd_iterate", "amgdd_solve", "amg_vcycle", "amg_vcycle_solve",
     "amgdd_residual_csr_noalloc", "amgdd_iterate_multi", "amgdd_solve_multi",
+    "amg_hybrid_cycle", "amg_hybrid_solve",
 ]
 
 _lib = None
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH):
         "amg_vcycle_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
         "amgdd_residual_csr_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
         "amgdd_iterate_multi": [vp, vp, vp, i32, vp],
+        "amg_hybrid_cycle": [vp, vp, vp, vp],
+        "amg_hybrid_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
         "amgdd_solve_multi": [vp, vp, vp, i32, f64, i32, vp, C.POINTER(amgdd_solve_info)],
     }
     for name, args in sig.items():
@@ -299,3 +302,11 @@ def amgdd_solve_multi(h, B, X, tol=1e-8, max_iter=200, stream=None, raise_on_noc
     return dict(iterations=k, converged=bool(info.converged), final_relres=info.final_relres,
                 history=hist.reshape(nrhs, max_iter + 1)[:, :k + 1].copy(), seconds=info.seconds,
                 kernel_launches=info.kernel_launches)
+
+
+def amg_hybrid_cycle(h, b, x, stream=None):
+    _check(load().amg_hybrid_cycle(h, _ptr(b), _ptr(x), _stream(stream)), h)
+
+
+def amg_hybrid_solve(h, b, x, tol=1e-8, max_iter=200, stream=None, raise_on_noconv=True):
+    return _solve(load().amg_hybrid_solve, h, b, x, tol, max_iter, stream, raise_on_noconv)

@@ -66,7 +66,7 @@ struct amgdd_handle_s {
         const double *b = nullptr;
         double *x = nullptr;
         int64_t launches = 0;
-    } graph[2];
+    } graph[3];
     cudaStream_t cap_stream = nullptr;
     // work space of the several-right-hand-side path, per width (2 or 4)
     struct Multi {
@@ -77,6 +77,12 @@ struct amgdd_handle_s {
     } multi[2];
     int64_t fac_rows = 0;
     FacParams fac_base{};
+    // hybrid AMG-DD (Algorithm 3): composite grids of the hierarchy from level
+    // hyb_level down, the residual of that level and its restrictions
+    int hyb_level = -1;
+    FacParams fac_hyb{};
+    double *r_hyb = nullptr;
+    std::vector<int64_t> hyb_off;
 };
 
 namespace {
@@ -223,6 +229,142 @@ amgdd_status require_device(amgdd_handle h)
 
 }  // namespace
 
+// Uploads one composite-grid layout (all grids, all levels of its hierarchy)
+// and fills the FAC kernel parameters; F's large arrays are released.
+static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, int nlev, int nsub, const std::vector<int64_t> &level_off,
+                              bool fp32, cudaStream_t st_, FacParams &P, const char **what)
+{
+    cudaError_t e;
+#define UP(x, y, msg)                                           \
+    do {                                                        \
+        if ((e = upload(h, x, y, st_)) != cudaSuccess) {        \
+            *what = msg;                                        \
+            return e;                                           \
+        }                                                       \
+    } while (0)
+    P.nlev = nlev;
+    P.nsub = nsub;
+    P.nfac = h->opt.n_fac;
+    P.nL = h->nL;
+    FacLevelDesc *dd;
+    int32_t *ord, *gm, *own;
+    int64_t *o0;
+    UP(F.desc, &dd, "upload desc");
+    UP(F.order, &ord, "upload order");
+    UP(F.gmap, &gm, "upload gmap");
+    P.fp32 = fp32 ? 1 : 0;
+    if (fp32) {
+        std::vector<float> l1f(F.l1inv.begin(), F.l1inv.end());
+        float *l1d;
+        UP(l1f, &l1d, "upload l1inv");
+        if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return e;
+        P.l1inv = l1d;
+    } else {
+        double *l1;
+        UP(F.l1inv, &l1, "upload l1inv");
+        P.l1inv = l1;
+    }
+    UP(F.owned, &own, "upload owned");
+    UP(F.owned0, &o0, "upload owned0");
+    P.col16 = F.A.c16 ? 1 : 0;
+    P.schedule = h->opt.schedule >= 1 && h->opt.schedule <= 9 ? h->opt.schedule : 8;
+    FacView *views[5] = {&F.A, &F.At, &F.AFc, &F.P, &F.R};
+    FacViewDev *dviews[5] = {&P.A, &P.At, &P.AFc, &P.P, &P.R};
+    for (int v = 0; v < 5; ++v) {
+        FacView &V = *views[v];
+        int64_t *so;
+        uint16_t *rl;
+        UP(V.soff, &so, "upload view slices");
+        UP(V.rlen, &rl, "upload view rows");
+        const void *va, *co;
+        if (V.v32) {
+            float *d;
+            UP(V.val32, &d, "upload view values");
+            va = d;
+        } else {
+            double *d;
+            UP(V.val64, &d, "upload view values");
+            va = d;
+        }
+        if (V.c16) {
+            uint16_t *c;
+            UP(V.col16, &c, "upload view columns");
+            co = c;
+        } else {
+            int32_t *c;
+            UP(V.col32, &c, "upload view columns");
+            co = c;
+        }
+        if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return e;
+        dviews[v]->soff = so;
+        dviews[v]->rlen = rl;
+        dviews[v]->col = co;
+        dviews[v]->val = va;
+        V = FacView();
+    }
+    // one bin per SM; grids by decreasing work into the lightest bin
+    {
+        int dev = 0, nsm = 1;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int nb = std::max(1, nsm);
+        std::vector<std::vector<int32_t>> bins((size_t)nb);
+        std::vector<int64_t> load((size_t)nb, 0);
+        for (int32_t g : F.order) {  // F.order: decreasing work
+            int best = 0;
+            for (int b = 1; b < nb; ++b)
+                if (load[b] < load[best]) best = b;
+            bins[best].push_back(g);
+            load[best] += F.work[g] > 0 ? F.work[g] : 1;
+        }
+        std::vector<int32_t> off(1, 0), grid;
+        for (auto &bv : bins) {
+            grid.insert(grid.end(), bv.begin(), bv.end());
+            off.push_back((int32_t)grid.size());
+        }
+        int32_t *doff, *dgrid, *dctr;
+        UP(off, &doff, "upload bins");
+        UP(grid, &dgrid, "upload bins");
+        if ((e = alloc(h, (size_t)nb, &dctr)) != cudaSuccess) {
+            *what = "alloc bin counters";
+            return e;
+        }
+        if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return e;
+        P.nbins = nb;
+        P.bin_off = doff;
+        P.bin_grid = dgrid;
+        P.ctr = dctr;
+    }
+    P.desc = dd;
+    P.order = ord;
+    P.gmap = gm;
+    P.owned = own;
+    P.owned0 = o0;
+    P.ainv = h->ainv;
+    for (int l = 0; l <= kMaxLevels; ++l) P.level_off[l] = l <= nlev ? level_off[l] : 0;
+    void *ws[6];
+    for (int k = 0; k < 6; ++k) {
+        if (fp32) {
+            float *w;
+            if ((e = alloc(h, (size_t)F.rows_total, &w)) != cudaSuccess) {
+                *what = "alloc FAC workspace";
+                return e;
+            }
+            ws[k] = w;
+        } else {
+            double *w;
+            if ((e = alloc(h, (size_t)F.rows_total, &w)) != cudaSuccess) {
+                *what = "alloc FAC workspace";
+                return e;
+            }
+            ws[k] = w;
+        }
+    }
+    P.u = ws[0]; P.f = ws[1]; P.t = ws[2]; P.s = ws[3]; P.w = ws[4]; P.d = ws[5];
+#undef UP
+    return cudaSuccess;
+}
+
 extern "C" {
 
 amgdd_status amgdd_options_default(amgdd_options *o)
@@ -238,6 +380,7 @@ amgdd_status amgdd_options_default(amgdd_options *o)
     o->threads = 0;
     o->schedule = 0;
     o->precision = 0;
+    o->hybrid_level = 0;
     return AMGDD_OK;
 }
 
@@ -320,6 +463,11 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             return fail(nullptr, hst == 1 ? AMGDD_ERR_SINGULAR : AMGDD_ERR_INVALID_ARG, why);
         }
         const int nlev = (int)h->H.lv.size();
+        if (h->opt.hybrid_level < 0 || h->opt.hybrid_level >= nlev) {
+            delete h;
+            return fail(nullptr, AMGDD_ERR_INVALID_ARG,
+                        "hybrid_level must be in [0, number of levels - 1] (" + std::to_string(nlev) + " levels)");
+        }
         std::vector<int> eta((size_t)nlev);
         for (int l = 0; l < nlev; ++l) eta[l] = padding[std::min(l, npadding - 1)];
         const int nth = host_threads();
@@ -378,6 +526,41 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
                 delete h;
                 return fail(nullptr, AMGDD_ERR_INVALID_ARG, "internal layout check failed: " + bad);
             }
+            // hybrid AMG-DD: composite grids of the hierarchy from level Lt down
+            FacLayout Fs;
+            int32_t hyb_ns = 0;
+            if (h->opt.hybrid_level > 0) {
+                // subdomains of level Lt: each C point keeps the subdomain of
+                // the point it comes from; subdomains left without points drop out
+                const int Lt = h->opt.hybrid_level;
+                std::vector<int32_t> pl(part, part + h->H.lv[0].A.rows);
+                for (int l = 0; l < Lt; ++l) {
+                    std::vector<int32_t> nx((size_t)h->H.lv[l + 1].A.rows);
+                    for (int32_t i = 0; i < h->H.lv[l].A.rows; ++i)
+                        if (h->H.lv[l].isC[i]) nx[h->H.lv[l].coarse[i]] = pl[i];
+                    pl.swap(nx);
+                }
+                std::vector<int32_t> remap((size_t)nsub, -1);
+                for (int32_t q : pl) remap[q] = 0;
+                for (int32_t p2 = 0; p2 < nsub; ++p2)
+                    if (remap[p2] == 0) remap[p2] = hyb_ns++;
+                for (int32_t &q : pl) q = remap[q];
+                Hierarchy Hs;
+                Hs.lv.assign(h->H.lv.begin() + Lt, h->H.lv.end());
+                Hs.ainv = h->H.ainv;
+                Composite Cs;
+                std::vector<int> etas(eta.begin() + Lt, eta.end());
+                build_composite(Hs, pl.data(), hyb_ns, etas, Cs, nth);
+                build_fac_layout(Hs, Cs, Fs, nth, false);
+                const std::string bad2 = validate_layouts(Hs, {}, Fs);
+                if (!bad2.empty()) {
+                    delete h;
+                    return fail(nullptr, AMGDD_ERR_INVALID_ARG, "internal hybrid layout check failed: " + bad2);
+                }
+                const int nls = nlev - Lt;
+                h->hyb_off.assign((size_t)nls + 1, 0);
+                for (int l = 0; l < nls; ++l) h->hyb_off[l + 1] = h->hyb_off[l] + Hs.lv[l].A.rows;
+            }
             if (h->opt.host_only == 2) goto done;
             auto bail = [&](cudaError_t e, const char *what) {
                 amgdd_status s2 = cuda_fail(nullptr, e, what);
@@ -422,120 +605,21 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             if ((e = cudaMallocHost((void **)&h->h_scal, 8 * sizeof(double))) != cudaSuccess)
                 return bail(e, "alloc pinned");
             // composite-grid layout
-            FacParams &P = h->fac;
-            P.nlev = nlev;
-            P.nsub = nsub;
-            P.nfac = h->opt.n_fac;
-            P.nL = h->nL;
-            FacLevelDesc *dd;
-            int32_t *ord, *gm, *own;
-            double *l1;
-            int64_t *o0;
-            if ((e = upload(h, F.desc, &dd, st_)) != cudaSuccess) return bail(e, "upload desc");
-            if ((e = upload(h, F.order, &ord, st_)) != cudaSuccess) return bail(e, "upload order");
-            if ((e = upload(h, F.gmap, &gm, st_)) != cudaSuccess) return bail(e, "upload gmap");
-            const bool fp32 = h->opt.precision == 1;
-            P.fp32 = fp32 ? 1 : 0;
-            if (fp32) {
-                std::vector<float> l1f(F.l1inv.begin(), F.l1inv.end());
-                float *l1d;
-                if ((e = upload(h, l1f, &l1d, st_)) != cudaSuccess) return bail(e, "upload l1inv");
-                if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload l1inv");
-                l1 = nullptr;
-                P.l1inv = l1d;
-            } else {
-                if ((e = upload(h, F.l1inv, &l1, st_)) != cudaSuccess) return bail(e, "upload l1inv");
-            }
-            if ((e = upload(h, F.owned, &own, st_)) != cudaSuccess) return bail(e, "upload owned");
-            if ((e = upload(h, F.owned0, &o0, st_)) != cudaSuccess) return bail(e, "upload owned0");
-            P.col16 = F.A.c16 ? 1 : 0;
-            P.schedule = h->opt.schedule >= 1 && h->opt.schedule <= 9 ? h->opt.schedule : 8;
-            FacView *views[5] = {&F.A, &F.At, &F.AFc, &F.P, &F.R};
-            FacViewDev *dviews[5] = {&P.A, &P.At, &P.AFc, &P.P, &P.R};
-            for (int v = 0; v < 5; ++v) {
-                FacView &V = *views[v];
-                int64_t *so;
-                uint16_t *rl;
-                if ((e = upload(h, V.soff, &so, st_)) != cudaSuccess) return bail(e, "upload view slices");
-                if ((e = upload(h, V.rlen, &rl, st_)) != cudaSuccess) return bail(e, "upload view rows");
-                const void *va, *co;
-                if (V.v32) {
-                    float *d;
-                    if ((e = upload(h, V.val32, &d, st_)) != cudaSuccess) return bail(e, "upload view values");
-                    va = d;
-                } else {
-                    double *d;
-                    if ((e = upload(h, V.val64, &d, st_)) != cudaSuccess) return bail(e, "upload view values");
-                    va = d;
-                }
-                if (V.c16) {
-                    uint16_t *c;
-                    if ((e = upload(h, V.col16, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
-                    co = c;
-                } else {
-                    int32_t *c;
-                    if ((e = upload(h, V.col32, &c, st_)) != cudaSuccess) return bail(e, "upload view columns");
-                    co = c;
-                }
-                if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload views");
-                dviews[v]->soff = so;
-                dviews[v]->rlen = rl;
-                dviews[v]->col = co;
-                dviews[v]->val = va;
-                V = FacView();
-            }
-            // one bin per SM; grids by decreasing work into the lightest bin
             {
-                int dev = 0, nsm = 1;
-                if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "device query");
-                if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-                    return bail(e, "device query");
-                const int nb = std::max(1, nsm);
-                std::vector<std::vector<int32_t>> bins((size_t)nb);
-                std::vector<int64_t> load((size_t)nb, 0);
-                for (int32_t g : F.order) {  // F.order: decreasing work
-                    int best = 0;
-                    for (int b = 1; b < nb; ++b)
-                        if (load[b] < load[best]) best = b;
-                    bins[best].push_back(g);
-                    load[best] += F.work[g] > 0 ? F.work[g] : 1;
-                }
-                std::vector<int32_t> off(1, 0), grid;
-                for (auto &bv : bins) {
-                    grid.insert(grid.end(), bv.begin(), bv.end());
-                    off.push_back((int32_t)grid.size());
-                }
-                int32_t *doff, *dgrid, *dctr;
-                if ((e = upload(h, off, &doff, st_)) != cudaSuccess) return bail(e, "upload bins");
-                if ((e = upload(h, grid, &dgrid, st_)) != cudaSuccess) return bail(e, "upload bins");
-                if ((e = alloc(h, (size_t)nb, &dctr)) != cudaSuccess) return bail(e, "alloc bin counters");
-                if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload bins");
-                P.nbins = nb;
-                P.bin_off = doff;
-                P.bin_grid = dgrid;
-                P.ctr = dctr;
+                const char *what = "";
+                if ((e = upload_fac(h, F, nlev, nsub, h->level_off, h->opt.precision == 1, st_, h->fac, &what)) !=
+                    cudaSuccess)
+                    return bail(e, what);
             }
-            P.desc = dd;
-            P.order = ord;
-            P.gmap = gm;
-            if (!fp32) P.l1inv = l1;
-            P.owned = own;
-            P.owned0 = o0;
-            P.ainv = h->ainv;
-            for (int l = 0; l <= kMaxLevels; ++l) P.level_off[l] = l <= nlev ? h->level_off[l] : 0;
-            void *ws[6];
-            for (int k = 0; k < 6; ++k) {
-                if (fp32) {
-                    float *w;
-                    if ((e = alloc(h, (size_t)F.rows_total, &w)) != cudaSuccess) return bail(e, "alloc FAC workspace");
-                    ws[k] = w;
-                } else {
-                    double *w;
-                    if ((e = alloc(h, (size_t)F.rows_total, &w)) != cudaSuccess) return bail(e, "alloc FAC workspace");
-                    ws[k] = w;
-                }
+            if (hyb_ns > 0) {
+                const int nls = nlev - h->opt.hybrid_level;
+                const char *what = "";
+                if ((e = upload_fac(h, Fs, nls, hyb_ns, h->hyb_off, false, st_, h->fac_hyb, &what)) != cudaSuccess)
+                    return bail(e, what);
+                if ((e = alloc(h, (size_t)h->hyb_off.back(), &h->r_hyb)) != cudaSuccess)
+                    return bail(e, "alloc hybrid residual");
+                h->hyb_level = h->opt.hybrid_level;
             }
-            P.u = ws[0]; P.f = ws[1]; P.t = ws[2]; P.s = ws[3]; P.w = ws[4]; P.d = ws[5];
             if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "setup upload");
             h->desc = F.desc;
             h->dev2map = F.dev2map;
@@ -702,6 +786,56 @@ static amgdd_status vcycle(amgdd_handle h, const double *b, double *x, cudaStrea
     return AMGDD_OK;
 }
 
+// Hybrid AMG-DD V(1,1)-cycle (Algorithm 3): the V-cycle's downsweep on levels
+// 0 .. Lt-1, one AMG-DD cycle on level Lt in place of the coarse solve, then
+// the V-cycle's upsweep.
+static amgdd_status vcycle_hybrid(amgdd_handle h, const double *b, double *x, cudaStream_t st)
+{
+    const int L = (int)h->lev.size() - 1;
+    const int Lt = h->hyb_level;
+    amgdd_status s;
+    for (int l = 0; l < Lt; ++l) {
+        DevLevel &D = h->lev[l];
+        double *u = l == 0 ? x : D.u;
+        const double *f = l == 0 ? b : D.f;
+        if ((s = relax(h, l, true, u, f, st)) != AMGDD_OK) return s;
+        if ((s = relax(h, l, false, u, f, st)) != AMGDD_OK) return s;
+        CK(launch_relax_compute(D.A, 0, D.n, f, u, D.l1inv, h->res, 1, st), "residual kernel");
+        CK(launch_spmv(D.R, 0, D.R.rows, h->res, h->lev[l + 1].f, 0, st), "restriction kernel");
+        CK(cudaMemsetAsync(h->lev[l + 1].u, 0, sizeof(double) * (size_t)h->lev[l + 1].n, st), "memset");
+        h->launches += 2;
+    }
+    {
+        // AMG-DD cycle on level Lt: r = f - A u, restrictions, AlgFAC on the
+        // composite grids of the sub-hierarchy, owned corrections into u
+        DevLevel &D = h->lev[Lt];
+        double *u = Lt == 0 ? x : D.u;
+        const double *f = Lt == 0 ? b : D.f;
+        CK(launch_relax_compute(D.A, 0, D.n, f, u, D.l1inv, h->r_hyb, 1, st), "residual kernel");
+        h->launches += 1;
+        for (int l = Lt; l < L; ++l) {
+            CK(launch_spmv(h->lev[l].R, 0, h->lev[l].R.rows, h->r_hyb + h->hyb_off[l - Lt],
+                           h->r_hyb + h->hyb_off[l - Lt + 1], 0, st), "restriction kernel");
+            h->launches += 1;
+        }
+        FacParams P = h->fac_hyb;
+        P.r_all = h->r_hyb;
+        P.x = u;
+        CK(launch_fac_all_grids(P, P.nsub, h->threads, st), "FAC kernel");
+        h->launches += 1;
+    }
+    for (int l = Lt - 1; l >= 0; --l) {
+        DevLevel &D = h->lev[l];
+        double *u = l == 0 ? x : D.u;
+        const double *f = l == 0 ? b : D.f;
+        CK(launch_spmv(D.P, 0, D.P.rows, h->lev[l + 1].u, u, 1, st), "interpolation kernel");
+        h->launches += 1;
+        if ((s = relax(h, l, false, u, f, st)) != AMGDD_OK) return s;
+        if ((s = relax(h, l, true, u, f, st)) != AMGDD_OK) return s;
+    }
+    return AMGDD_OK;
+}
+
 amgdd_status amgdd_residual(amgdd_handle h, const double *b, const double *x, double *r, double *nrm2, void *stream)
 {
     amgdd_status s = require_device(h);
@@ -785,9 +919,10 @@ amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream
 // Captures one solver iteration (the AMG-DD or V-cycle update followed by
 // the residual of the new iterate and the copy of its squared norm into
 // pinned host memory) as a CUDA graph on a private stream.
-static amgdd_status capture_iteration(amgdd_handle h, bool amgdd, const double *b, double *x)
+static amgdd_status capture_iteration(amgdd_handle h, int method, const double *b, double *x)
 {
-    auto &G = h->graph[amgdd ? 0 : 1];
+    const bool amgdd = method == 0;
+    auto &G = h->graph[method];
     if (G.exec && G.b == b && G.x == x) return AMGDD_OK;
     if (G.exec) {
         cudaGraphExecDestroy(G.exec);
@@ -797,7 +932,8 @@ static amgdd_status capture_iteration(amgdd_handle h, bool amgdd, const double *
     cudaStream_t cs = h->cap_stream;
     const int64_t l0 = h->launches;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
-    amgdd_status s = amgdd ? restrict_all(h, h->r_all, cs) : vcycle(h, b, x, cs);
+    amgdd_status s = amgdd ? restrict_all(h, h->r_all, cs)
+                           : method == 1 ? vcycle(h, b, x, cs) : vcycle_hybrid(h, b, x, cs);
     if (s == AMGDD_OK && amgdd) s = fac(h, h->r_all, x, cs);
     if (s == AMGDD_OK) {
         cudaError_t e = launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs);
@@ -824,13 +960,13 @@ static amgdd_status capture_iteration(amgdd_handle h, bool amgdd, const double *
 }
 
 static amgdd_status solve_loop(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
-                               cudaStream_t st, amgdd_solve_info *info, bool amgdd)
+                               cudaStream_t st, amgdd_solve_info *info, int method)
 {
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t l0 = h->launches;
     amgdd_status s;
-    if ((s = capture_iteration(h, amgdd, b, x)) != AMGDD_OK) return s;
-    const auto &G = h->graph[amgdd ? 0 : 1];
+    if ((s = capture_iteration(h, method, b, x)) != AMGDD_OK) return s;
+    const auto &G = h->graph[method];
     CK(launch_sumsq(b, h->lev[0].n, h->partial, h->nred, h->scal + 1, st), "norm kernel");
     h->launches += 2;
     CK(cudaMemcpyAsync(h->h_scal + 1, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
@@ -1012,7 +1148,7 @@ amgdd_status amgdd_solve(amgdd_handle h, const double *b, double *x, double tol,
     if (s != AMGDD_OK) return s;
     if (!b || !x || max_iter < 0 || !(tol >= 0.0)) return fail(h, AMGDD_ERR_INVALID_ARG, "bad solve arguments");
     h->last_stream = (cudaStream_t)stream;
-    return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, true);
+    return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, 0);
 }
 
 amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
@@ -1022,7 +1158,28 @@ amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double
     if (s != AMGDD_OK) return s;
     if (!b || !x || max_iter < 0 || !(tol >= 0.0)) return fail(h, AMGDD_ERR_INVALID_ARG, "bad solve arguments");
     h->last_stream = (cudaStream_t)stream;
-    return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, false);
+    return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, 1);
+}
+
+amgdd_status amg_hybrid_cycle(amgdd_handle h, const double *b, double *x, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!b || !x) return fail(h, AMGDD_ERR_INVALID_ARG, "null vector");
+    if (h->hyb_level < 0) return fail(h, AMGDD_ERR_INVALID_ARG, "handle was set up without hybrid_level");
+    h->last_stream = (cudaStream_t)stream;
+    return vcycle_hybrid(h, b, x, (cudaStream_t)stream);
+}
+
+amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                              void *stream, amgdd_solve_info *info)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!b || !x || max_iter < 0 || !(tol >= 0.0)) return fail(h, AMGDD_ERR_INVALID_ARG, "bad solve arguments");
+    if (h->hyb_level < 0) return fail(h, AMGDD_ERR_INVALID_ARG, "handle was set up without hybrid_level");
+    h->last_stream = (cudaStream_t)stream;
+    return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, 2);
 }
 
 }  // extern "C"

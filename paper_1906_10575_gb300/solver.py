@@ -15,7 +15,7 @@ class Solver:
 
     def __init__(self, rowptr, col, val, part, nsub, padding=1, n_fac=2, theta=0.25,
                  max_coarse=16, max_levels=25, host_only=False, threads=0, schedule=0, precision=0,
-                 stream=None):
+                 hybrid_level=0, stream=None):
         o = capi.amgdd_options_default()
         o.n_fac = n_fac
         o.theta = theta
@@ -25,6 +25,7 @@ class Solver:
         o.threads = threads
         o.schedule = schedule
         o.precision = precision
+        o.hybrid_level = hybrid_level
         self.n = len(rowptr) - 1
         self.h = capi.amgdd_setup(rowptr, col, val, part, nsub, padding, o, stream)
         self.stats = capi.amgdd_get_stats(self.h)
@@ -53,3 +54,7 @@ class Solver:
     def solve_multi(self, B, X, tol=1e-8, max_iter=200, stream=None):
         """All columns of B / X (device tensors of shape (n, 2) or (n, 4))."""
         return capi.amgdd_solve_multi(self.h, B, X, tol, max_iter, stream)
+
+    def hybrid_solve(self, b, x, tol=1e-8, max_iter=200, stream=None):
+        """Hybrid AMG-DD (set up with hybrid_level >= 1)."""
+        return capi.amg_hybrid_solve(self.h, b, x, tol, max_iter, stream)

@@ -260,3 +260,28 @@ def test_multi_rhs_columns_equal_single_column_solves(case, nrhs, precision):
         assert np.allclose(info["history"][j], ho, rtol=1e-12, atol=0), j
     assert info["converged"] and info["history"][:, -1].max() <= 1e-8
     s.close()
+
+
+@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d", "ragged2d"])
+def test_hybrid_amgdd_bit_exact(case):
+    """Hybrid AMG-DD (Algorithm 3) on every switch level equals the oracle's
+    hybrid cycle; switching on the coarsest level is the plain V-cycle."""
+    rp, ci, v, part, nsub, pad, b = _case(case)
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    L = o.nlev - 1
+    x0 = np.random.default_rng(9).standard_normal(o.n)
+    for lt in range(1, L + 1):
+        s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, hybrid_level=lt)
+        x = _dev(x0)
+        capi.amg_hybrid_cycle(s.h, _dev(b), x)
+        ref = o.hybrid_apply(lt, b, x0, 2)
+        assert np.array_equal(_host(x), ref), lt
+        if lt == L:
+            assert np.array_equal(ref, o.vcycle_apply(b, x0))
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        info = s.hybrid_solve(_dev(b), x, tol=1e-8, max_iter=200)
+        xo, ho = o.hybrid_solve(lt, b, 2, tol=1e-8, maxit=200)
+        assert info["iterations"] == len(ho) - 1, lt
+        assert np.array_equal(_host(x), xo), lt
+        assert np.allclose(info["history"], ho, rtol=1e-12, atol=0), lt
+        s.close()

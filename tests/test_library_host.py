@@ -111,3 +111,17 @@ def test_validation_errors():
     with pytest.raises(capi.AmgddError) as e:       # no device side
         capi.amgdd_iterate(s.h, None, None)
     assert e.value.status in (1, 9)
+
+
+def test_hybrid_layouts_validate_on_host():
+    """The composite grids of every sub-hierarchy (hybrid AMG-DD, Algorithm 3)
+    pass the device-index range checks without a GPU; bad levels are refused."""
+    rp, ci, v = I.poisson3d(20, 20, 20)
+    part, nsub = I.box_partition((20, 20, 20), (10, 10, 5))
+    s0 = Solver(rp, ci, v, part, nsub, 2, host_only=1)
+    for lt in range(1, s0.nlev):
+        s = Solver(rp, ci, v, part, nsub, 2, host_only=2, hybrid_level=lt)
+        s.close()
+    with pytest.raises(capi.AmgddError) as e:
+        Solver(rp, ci, v, part, nsub, 2, host_only=2, hybrid_level=s0.nlev)
+    assert e.value.status == 1

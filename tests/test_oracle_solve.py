@@ -157,3 +157,19 @@ def test_mixed_precision_refinement_converges_to_fp64_solution():
     assert abs(len(hm) - len(h64)) <= 2
     # early iterations: the FP32 correction is as good as the FP64 one
     assert np.allclose(hm[:4], h64[:4], rtol=1e-4)
+
+
+def test_hybrid_limits_and_convergence():
+    """Algorithm 3: switching to AMG-DD on level 0 is the AMG-DD iteration;
+    switching on the coarsest level (stored whole in every composite grid)
+    is the plain V-cycle; in between the cycle still solves the system."""
+    o, A, b = _problem2d(40, 36, (10, 9), 1, seed=4)
+    x0 = np.random.default_rng(1).standard_normal(o.n)
+    assert np.array_equal(o.hybrid_apply(0, b, x0, 2), o.amgdd_iteration(b, x0, 2))
+    L = o.nlev - 1
+    assert np.array_equal(o.hybrid_apply(L, b, x0, 2), o.vcycle_apply(b, x0))
+    xd = np.linalg.solve(A.toarray(), b)
+    for lev0 in (1, 2):
+        x, h = o.hybrid_solve(lev0, b, 2, tol=1e-12)
+        assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+        assert np.all(np.diff(h) < 0)

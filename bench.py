@@ -262,6 +262,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the four-right-hand-side measurement")
+    ap.add_argument("--hybrid-level", type=int, default=2,
+                    help="switch level of the hybrid AMG-DD measurement (0 = skip)")
     ap.add_argument("--schedule", type=int, default=0, help="FAC kernel variant (0 = library default)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid edge (default 128, the benchmark workload; smaller edges "
@@ -401,6 +403,20 @@ def main():
                  "dtype": "f32 AlgFAC / f64 refinement"}
         sm.close()
 
+    # hybrid AMG-DD (Algorithm 3): V-cycle on the fine levels, one AMG-DD
+    # cycle on level --hybrid-level
+    hybrid = None
+    if args.hybrid_level > 0:
+        sh = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                    hybrid_level=args.hybrid_level, stream=stream)
+        with torch.cuda.stream(stream):
+            timed(sh.hybrid_solve, args.warmup)
+            t_h, i_h = timed(sh.hybrid_solve, args.steps)
+        ms_h = max_over_ranks([statistics.median(t_h)], dist)[0]
+        hybrid = {"level": args.hybrid_level, "ms": round(ms_h, 3), "iterations": i_h[-1]["iterations"],
+                  "final_relres": i_h[-1]["final_relres"]}
+        sh.close()
+
     # four right-hand sides of the same matrix at once (FP64): every operator
     # entry feeds four fma chains
     multi = None
@@ -493,6 +509,7 @@ def main():
         "clocks": clocks,
         "mixed_precision": mixed,
         "multi_rhs": multi,
+        "hybrid": hybrid,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, it_dd)

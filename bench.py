@@ -262,7 +262,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the four-right-hand-side measurement")
-    ap.add_argument("--hybrid-level", type=int, default=2,
+    ap.add_argument("--hybrid-level", type=int, default=6,
                     help="switch level of the hybrid AMG-DD measurement (0 = skip)")
     ap.add_argument("--schedule", type=int, default=0, help="FAC kernel variant (0 = library default)")
     ap.add_argument("--n", type=int, default=128,

@@ -123,6 +123,33 @@ def checkerboard_kappa(n: int, blocks: int, seed: int, values=(1.0, 1e3)):
     return np.ascontiguousarray(k[:n, :n, :n])
 
 
+def gaussian_random_field(n: int, length: float = 0.1, variance: float = 1.0, seed: int = 0):
+    """Zero-mean Gaussian random field on the interior nodes of the unit cube
+    (h = 1/(n+1)), shape (n, n, n): white noise smoothed by a separable
+    Gaussian filter whose covariance exp(-d^2 / (2 length^2)) corresponds to a
+    filter width length / sqrt(2) per axis, renormalised to the requested
+    variance (sample variance)."""
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal((n, n, n))
+    h = 1.0 / (n + 1)
+    sigma = length / np.sqrt(2.0) / h            # in grid points
+    r = int(np.ceil(4 * sigma))
+    t = np.arange(-r, r + 1)
+    k = np.exp(-0.5 * (t / sigma) ** 2)
+    k /= k.sum()
+    g = noise
+    for ax in range(3):
+        g = np.apply_along_axis(lambda v: np.convolve(v, k, mode="same"), ax, g)
+    g -= g.mean()
+    g *= np.sqrt(variance / g.var())
+    return g
+
+
+def lognormal_kappa(n: int, length: float = 0.1, variance: float = 1.0, seed: int = 0):
+    """kappa = exp(g) with g a Gaussian random field (gaussian_random_field)."""
+    return np.exp(gaussian_random_field(n, length, variance, seed))
+
+
 def box_partition(shape, box):
     """Subdomain id of every unknown for a partition into boxes.
 

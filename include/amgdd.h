@@ -253,6 +253,19 @@ amgdd_status amgdd_iterate_multi(amgdd_handle h, const double *B, double *X, int
 amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, double tol,
                                int32_t max_iter, void *stream, amgdd_solve_info *info);
 
+/* ---- adjoint: gradient with respect to diffusion coefficients -------------
+ * The paper has no adjoint; this supports differentiating solves of the 3D
+ * 7-point diffusion operator -div(kappa grad u) with node-wise kappa, face
+ * coefficients 2 k_i k_j / (k_i + k_j) and Dirichlet faces using k_i
+ * (lexicographic numbering, i fastest). For vectors x, lam it computes
+ *   grad[m] = d(-lam^T A(kappa) x)/d kappa_m
+ *           = -( sum over neighbours j of m of 2 k_j^2/(k_m + k_j)^2 (lam_m - lam_j)(x_m - x_j)
+ *                + (boundary faces of m) lam_m x_m ),
+ * which is dL/dkappa when x solves A x = b and lam solves A lam = dL/dx.
+ * kappa, x, lam, grad: DEVICE, nx*ny*nz doubles each; stream-ordered. */
+amgdd_status amgdd_kappa_grad_3d(int32_t nx, int32_t ny, int32_t nz, const double *kappa, const double *x,
+                                 const double *lam, double *grad, void *stream);
+
 /* ---- residual without any device allocation ------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * cannot call cudaMalloc at the moment they need a residual, for example code

@@ -302,3 +302,36 @@ class Oracle:
         k = self.lib.orc_hybrid_solve(self.h, hs, cs, int(lev0), int(nfac), _c64(b), x, float(tol),
                                       int(maxit), hist)
         return x, hist[:k + 1]
+
+
+def kappa_gradient(kappa, x, lam):
+    """d(-lam^T A(kappa) x)/d kappa for the 3D 7-point diffusion operator with
+    harmonic-mean faces 2 k_i k_j/(k_i + k_j) and Dirichlet faces using k_i.
+
+    lam^T A x = sum over interior faces c_f (lam_i - lam_j)(x_i - x_j)
+              + sum over boundary faces of i of k_i lam_i x_i,
+    dc_f/dk_i = 2 k_j^2 / (k_i + k_j)^2. kappa: (nz, ny, nx); x, lam: flat,
+    lexicographic (i fastest). Plain per-axis loops over the faces."""
+    k = np.asarray(kappa, np.float64)
+    X = np.asarray(x, np.float64).reshape(k.shape)
+    Lm = np.asarray(lam, np.float64).reshape(k.shape)
+    g = np.zeros_like(k)
+    nb = np.zeros_like(k)
+    for ax in range(3):
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        lo, hi = tuple(lo), tuple(hi)
+        ka, kb = k[lo], k[hi]
+        prod = (Lm[lo] - Lm[hi]) * (X[lo] - X[hi])
+        g[lo] += 2 * kb * kb / ((ka + kb) ** 2) * prod
+        g[hi] += 2 * ka * ka / ((ka + kb) ** 2) * prod
+        first = [slice(None)] * 3
+        last = [slice(None)] * 3
+        first[ax] = 0
+        last[ax] = -1
+        nb[tuple(first)] += 1
+        nb[tuple(last)] += 1
+    g += nb * Lm * X
+    return -g.reshape(-1)

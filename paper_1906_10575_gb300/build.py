@@ -19,7 +19,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
-CU_SOURCES = ["kernels.cu", "kernels_multi.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels.cu", "kernels_multi.cu", "adjoint.cu", "noalloc.cu"]
 CXX_SOURCES = ["hierarchy.cpp", "composite.cpp", "capi.cpp"]
 
 

@@ -62,7 +62,7 @@ EXPORTS = [
     "amgdd_get_coarse_inverse", "amgdd_residual", "amgdd_restrict", "amgdd_fac",
     "amgdd_get_fac_state", "amgdd_iterate", "amgdd_solve", "amg_vcycle", "amg_vcycle_solve",
     "amgdd_residual_csr_noalloc", "amgdd_iterate_multi", "amgdd_solve_multi",
-    "amg_hybrid_cycle", "amg_hybrid_solve",
+    "amg_hybrid_cycle", "amg_hybrid_solve", "amgdd_kappa_grad_3d",
 ]
 
 _lib = None
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         "amgdd_residual_csr_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
         "amgdd_iterate_multi": [vp, vp, vp, i32, vp],
         "amg_hybrid_cycle": [vp, vp, vp, vp],
+        "amgdd_kappa_grad_3d": [i32, i32, i32, vp, vp, vp, vp, vp],
         "amg_hybrid_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
         "amgdd_solve_multi": [vp, vp, vp, i32, f64, i32, vp, C.POINTER(amgdd_solve_info)],
     }
@@ -310,3 +311,11 @@ def amg_hybrid_cycle(h, b, x, stream=None):
 
 def amg_hybrid_solve(h, b, x, tol=1e-8, max_iter=200, stream=None, raise_on_noconv=True):
     return _solve(load().amg_hybrid_solve, h, b, x, tol, max_iter, stream, raise_on_noconv)
+
+
+def amgdd_kappa_grad_3d(shape, kappa, x, lam, grad, stream=None):
+    """grad = d(-lam^T A(kappa) x)/d kappa for the 3D diffusion operator
+    (shape = (nx, ny, nz); all arrays device tensors of nx*ny*nz doubles)."""
+    nx, ny, nz = (int(v) for v in shape)
+    _check(load().amgdd_kappa_grad_3d(nx, ny, nz, _ptr(kappa), _ptr(x), _ptr(lam), _ptr(grad),
+                                      _stream(stream)))

@@ -172,6 +172,40 @@ def box_partition(shape, box):
     return part.astype(np.int32), int(mult)
 
 
+def batched_poisson(nsys: int = 64, edges=(32, 48, 64, 80, 96), box: int = 16, nrhs: int = 4, seed: int = 0):
+    """Independent 3D 7-point Poisson systems as one block-diagonal matrix.
+
+    Each system's edge length is drawn uniformly from `edges` (seeded); its
+    unknowns are partitioned into boxes of `box`^3 (uneven boxes at the ends
+    when box does not divide the edge), numbered after the previous systems'.
+    Returns rowptr, col, val (int32/int32/float64), part (int32), nsub,
+    B (n x nrhs, U[-1,1] from the seed), the edge list and the row offsets."""
+    rng = np.random.default_rng(seed)
+    picks = [int(edges[i]) for i in rng.integers(0, len(edges), size=nsys)]
+    rps, cis, vs, parts = [], [], [], []
+    row0 = 0
+    nnz0 = 0
+    sub0 = 0
+    offs = [0]
+    for e in picks:
+        rp, ci, v = poisson3d(e, e, e)
+        part, ns = box_partition((e, e, e), (box, box, box))
+        rps.append(rp[:-1].astype(np.int64) + nnz0)
+        cis.append(ci.astype(np.int64) + row0)
+        vs.append(v)
+        parts.append(part.astype(np.int64) + sub0)
+        row0 += len(rp) - 1
+        nnz0 += len(ci)
+        sub0 += ns
+        offs.append(row0)
+    rowptr = np.concatenate(rps + [np.array([nnz0], np.int64)])
+    if nnz0 >= 2**31:
+        raise ValueError("batch too large for int32 row pointers")
+    B = rng.uniform(-1.0, 1.0, size=(row0, nrhs))
+    return (rowptr.astype(np.int32), np.concatenate(cis).astype(np.int32), np.concatenate(vs),
+            np.concatenate(parts).astype(np.int32), int(sub0), B, picks, np.array(offs))
+
+
 def uniform_rhs(n: int, seed: int):
     """b ~ U[-1, 1] from numpy.random.default_rng(seed)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)

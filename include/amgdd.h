@@ -66,7 +66,11 @@ typedef struct {
     int32_t host_only;      /* 1: build hierarchy and maps on the host only, no
                                device upload (inspection / CPU testing);
                                2: also build and range-check the device layouts,
-                               still without touching the device */
+                               still without touching the device, holding the
+                               composite-grid layout whole on the host;
+                               3: as 2, but the composite-grid layout is packed,
+                               checked and dropped chunk by chunk, the way a
+                               device setup streams it to the device */
     int32_t threads;        /* FAC kernel threads per block (0 = default 512) */
     int32_t schedule;       /* FAC kernel variant, all giving identical results:
                                0 = default (8); 1 = four resident blocks of 512

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "kernels.cuh"
@@ -99,14 +100,27 @@ struct FacView {
     std::vector<float> val32;
     bool c16 = true, v32 = false;
     int64_t entries = 0;                  // stored (non-padding) entries
-    size_t size() const { return c16 ? col16.size() : col32.size(); }
-    int32_t col(size_t i) const { return c16 ? (int32_t)col16[i] : col32[i]; }
+    // A streamed layout hands each packed chunk on and drops it: base, sbase
+    // and rbase count the entries, slice offsets and rows already handed on,
+    // so soff values, desc slice indices and row indices stay absolute.
+    int64_t base = 0, sbase = 0, rbase = 0;
+    size_t size() const { return c16 ? col16.size() : col32.size(); }   // entries held
+    int64_t total() const { return base + (int64_t)size(); }
+    int32_t col(size_t i) const { return c16 ? (int32_t)col16[i] : col32[i]; }   // held index
+    void flush()
+    {
+        base = total();
+        sbase += (int64_t)soff.size();
+        rbase += (int64_t)rlen.size();
+        soff.clear(); rlen.clear(); col16.clear(); col32.clear(); val64.clear(); val32.clear();
+    }
 };
 struct FacLayout {
     int nlev = 0, nsub = 0;
     std::vector<FacLevelDesc> desc;       // [p * nlev + l]
     std::vector<int32_t> gmap;            // local -> level index
     std::vector<double> l1inv;            // per row (real rows used)
+    int64_t row_base = 0;                 // rows of gmap / l1inv already handed on
     FacView A, At, AFc, P, R;
     std::vector<int32_t> owned;           // level-0 local indices of owned points
     std::vector<int64_t> owned0;          // per grid offset into owned (nsub+1)
@@ -121,10 +135,25 @@ struct FacLayout {
     std::vector<int64_t> lvA, lvAt, lvAFc, lvP, lvR;
 };
 
-void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads, bool fp32);
+// Called after each chunk of grids [p0, p0 + pn) has been packed into F; a
+// consumer that streams the layout checks the chunk, copies it away and calls
+// flush() on the views (and advances row_base). A non-empty return aborts the
+// build with that message.
+using FacSink = std::function<std::string(FacLayout &F, int p0, int pn)>;
+
+// Packs the composite-grid layout; without a sink F ends up holding all of it.
+// Returns the sink's error, or an empty string.
+std::string build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads, bool fp32,
+                             const FacSink &sink = FacSink());
 void build_global_dev(const Hierarchy &H, std::vector<GlobalLevelDev> &G);
 
 // Range checks of every index the kernels will dereference; empty if valid.
+std::string validate_global(const Hierarchy &H, const std::vector<GlobalLevelDev> &G);
+// the grids [p0, p0 + pn) of F, whose rows and slices F still holds
+std::string validate_fac_grids(const Hierarchy &H, const FacLayout &F, int p0, int pn);
+// row totals of the views and the launch order, once all grids are packed
+std::string validate_fac_totals(const FacLayout &F);
+// all of the above for a layout held whole
 std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDev> &G, const FacLayout &F);
 
 }  // namespace amgdd

@@ -227,12 +227,138 @@ amgdd_status require_device(amgdd_handle h)
     return AMGDD_OK;
 }
 
+// A device array appended to from the host; its capacity doubles, the old
+// contents moving by a device-to-device copy.
+struct DevGrow {
+    char *d = nullptr;
+    size_t n = 0, cap = 0;
+};
+
+// The large arrays of a composite-grid layout (five views, the map to level
+// indices and the l1 weights), filled on the device chunk by chunk while the
+// layout is packed: each chunk is range-checked, appended and dropped on the
+// host, so the host holds one chunk of the layout at a time.
+struct FacStream {
+    DevGrow soff[5], rlen[5], col[5], val[5], gmap, l1inv;
+    bool fp32 = false;
+    bool host = false;              // check and drop only (no device)
+    cudaError_t err = cudaSuccess;
+    const char *what = "";
+    std::vector<float> l1f;
+
+    DevGrow *all(int k)
+    {
+        if (k < 5) return &soff[k];
+        if (k < 10) return &rlen[k - 5];
+        if (k < 15) return &col[k - 10];
+        if (k < 20) return &val[k - 15];
+        return k == 20 ? &gmap : &l1inv;
+    }
+    ~FacStream()
+    {
+        for (int k = 0; k < 22; ++k)
+            if (all(k)->d) cudaFree(all(k)->d);
+    }
+    cudaError_t append(DevGrow &g, const void *src, size_t bytes, cudaStream_t st)
+    {
+        cudaError_t e;
+        if (g.n + bytes > g.cap) {
+            const size_t nc = std::max({g.cap * 2, g.n + bytes, (size_t)1 << 20});
+            void *p = nullptr;
+            if ((e = cudaMalloc(&p, nc)) != cudaSuccess) return e;
+            if (g.n && (e = cudaMemcpyAsync(p, g.d, g.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) {
+                cudaFree(p);
+                return e;
+            }
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                cudaFree(p);
+                return e;
+            }
+            if (g.d) cudaFree(g.d);
+            g.d = static_cast<char *>(p);
+            g.cap = nc;
+        }
+        if (bytes && (e = cudaMemcpyAsync(g.d + g.n, src, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+        g.n += bytes;
+        return cudaSuccess;
+    }
+    template <class T>
+    cudaError_t app(DevGrow &g, const std::vector<T> &v, cudaStream_t st)
+    {
+        return append(g, v.data(), v.size() * sizeof(T), st);
+    }
+    // Sink body: check grids [p0, p0 + pn), append what F holds, drop it.
+    std::string consume(const Hierarchy &H, FacLayout &F, int p0, int pn, cudaStream_t st)
+    {
+        std::string bad = validate_fac_grids(H, F, p0, pn);
+        if (!bad.empty()) return bad;
+        FacView *views[5] = {&F.A, &F.At, &F.AFc, &F.P, &F.R};
+        cudaError_t e = cudaSuccess;
+        for (int v = 0; v < 5 && e == cudaSuccess && !host; ++v) {
+            FacView &V = *views[v];
+            what = "upload view slices";
+            if ((e = app(soff[v], V.soff, st)) != cudaSuccess) break;
+            what = "upload view rows";
+            if ((e = app(rlen[v], V.rlen, st)) != cudaSuccess) break;
+            what = "upload view columns";
+            if ((e = V.c16 ? app(col[v], V.col16, st) : app(col[v], V.col32, st)) != cudaSuccess) break;
+            what = "upload view values";
+            if ((e = V.v32 ? app(val[v], V.val32, st) : app(val[v], V.val64, st)) != cudaSuccess) break;
+        }
+        if (e == cudaSuccess && !host) {
+            what = "upload gmap";
+            e = app(gmap, F.gmap, st);
+        }
+        if (e == cudaSuccess && !host) {
+            what = "upload l1inv";
+            if (fp32) {
+                l1f.assign(F.l1inv.begin(), F.l1inv.end());
+                e = app(l1inv, l1f, st);
+            } else {
+                e = app(l1inv, F.l1inv, st);
+            }
+        }
+        // the host vectors are reused by the next chunk
+        if (e == cudaSuccess && !host) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            err = e;
+            return std::string(what) + ": " + cudaGetErrorString(e);
+        }
+        for (FacView *V : views) V->flush();
+        F.row_base += (int64_t)F.gmap.size();
+        F.gmap.clear();
+        F.l1inv.clear();
+        return "";
+    }
+};
+
+// Moves a grown array into an exact-size allocation owned by the handle.
+cudaError_t settle(amgdd_handle h, DevGrow &g, cudaStream_t st, void **out)
+{
+    *out = nullptr;
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(g.n, 16);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(p);
+    h->dev_bytes += (int64_t)bytes;
+    if (g.n && (e = cudaMemcpyAsync(p, g.d, g.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    cudaFree(g.d);
+    g = DevGrow();
+    *out = p;
+    return cudaSuccess;
+}
+
 }  // namespace
 
-// Uploads one composite-grid layout (all grids, all levels of its hierarchy)
-// and fills the FAC kernel parameters; F's large arrays are released.
-static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, int nlev, int nsub, const std::vector<int64_t> &level_off,
-                              bool fp32, cudaStream_t st_, FacParams &P, const char **what)
+// Fills the FAC kernel parameters of one composite-grid layout (all grids,
+// all levels of its hierarchy): the views, map and l1 weights already streamed
+// to the device by S, the small per-grid tables, the per-SM bins and the
+// work space.
+static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, FacStream &S, int nlev, int nsub,
+                              const std::vector<int64_t> &level_off, bool fp32, cudaStream_t st_, FacParams &P,
+                              const char **what)
 {
     cudaError_t e;
 #define UP(x, y, msg)                                           \
@@ -247,61 +373,32 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, int nlev, int nsub, 
     P.nfac = h->opt.n_fac;
     P.nL = h->nL;
     FacLevelDesc *dd;
-    int32_t *ord, *gm, *own;
+    int32_t *ord, *own;
     int64_t *o0;
     UP(F.desc, &dd, "upload desc");
     UP(F.order, &ord, "upload order");
-    UP(F.gmap, &gm, "upload gmap");
     P.fp32 = fp32 ? 1 : 0;
-    if (fp32) {
-        std::vector<float> l1f(F.l1inv.begin(), F.l1inv.end());
-        float *l1d;
-        UP(l1f, &l1d, "upload l1inv");
-        if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return e;
-        P.l1inv = l1d;
-    } else {
-        double *l1;
-        UP(F.l1inv, &l1, "upload l1inv");
-        P.l1inv = l1;
-    }
     UP(F.owned, &own, "upload owned");
     UP(F.owned0, &o0, "upload owned0");
     P.col16 = F.A.c16 ? 1 : 0;
     P.schedule = h->opt.schedule >= 1 && h->opt.schedule <= 9 ? h->opt.schedule : 8;
-    FacView *views[5] = {&F.A, &F.At, &F.AFc, &F.P, &F.R};
     FacViewDev *dviews[5] = {&P.A, &P.At, &P.AFc, &P.P, &P.R};
+    void *gm = nullptr, *l1 = nullptr;
+    *what = "settle layout";
     for (int v = 0; v < 5; ++v) {
-        FacView &V = *views[v];
-        int64_t *so;
-        uint16_t *rl;
-        UP(V.soff, &so, "upload view slices");
-        UP(V.rlen, &rl, "upload view rows");
-        const void *va, *co;
-        if (V.v32) {
-            float *d;
-            UP(V.val32, &d, "upload view values");
-            va = d;
-        } else {
-            double *d;
-            UP(V.val64, &d, "upload view values");
-            va = d;
-        }
-        if (V.c16) {
-            uint16_t *c;
-            UP(V.col16, &c, "upload view columns");
-            co = c;
-        } else {
-            int32_t *c;
-            UP(V.col32, &c, "upload view columns");
-            co = c;
-        }
-        if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return e;
-        dviews[v]->soff = so;
-        dviews[v]->rlen = rl;
+        void *so, *rl, *co, *va;
+        if ((e = settle(h, S.soff[v], st_, &so)) != cudaSuccess) return e;
+        if ((e = settle(h, S.rlen[v], st_, &rl)) != cudaSuccess) return e;
+        if ((e = settle(h, S.col[v], st_, &co)) != cudaSuccess) return e;
+        if ((e = settle(h, S.val[v], st_, &va)) != cudaSuccess) return e;
+        dviews[v]->soff = static_cast<const int64_t *>(so);
+        dviews[v]->rlen = static_cast<const uint16_t *>(rl);
         dviews[v]->col = co;
         dviews[v]->val = va;
-        V = FacView();
     }
+    if ((e = settle(h, S.gmap, st_, &gm)) != cudaSuccess) return e;
+    if ((e = settle(h, S.l1inv, st_, &l1)) != cudaSuccess) return e;
+    P.l1inv = l1;
     // one bin per SM; grids by decreasing work into the lightest bin
     {
         int dev = 0, nsm = 1;
@@ -337,7 +434,7 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, int nlev, int nsub, 
     }
     P.desc = dd;
     P.order = ord;
-    P.gmap = gm;
+    P.gmap = static_cast<const int32_t *>(gm);
     P.owned = own;
     P.owned0 = o0;
     P.ainv = h->ainv;
@@ -507,8 +604,23 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
         if (h->opt.host_only != 1) {
             cudaStream_t st_ = (cudaStream_t)stream;
             h->last_stream = st_;
+            // with a device, the layout goes to it chunk by chunk as it is
+            // packed; host_only = 3 packs, checks and drops it the same way
+            const bool to_dev = h->opt.host_only == 0 || h->opt.host_only == 3;
             FacLayout F;
-            build_fac_layout(h->H, h->C, F, nth, h->opt.precision == 1);
+            FacStream FS;
+            FS.fp32 = h->opt.precision == 1;
+            FS.host = h->opt.host_only == 3;
+            FacSink sink;
+            if (to_dev) sink = [&](FacLayout &Lf, int p0, int pn) { return FS.consume(h->H, Lf, p0, pn, st_); };
+            std::string badf = build_fac_layout(h->H, h->C, F, nth, h->opt.precision == 1, sink);
+            if (badf.empty()) badf = to_dev ? validate_fac_totals(F) : validate_layouts(h->H, {}, F);
+            if (!badf.empty()) {
+                const cudaError_t fe = FS.err;
+                delete h;
+                if (fe != cudaSuccess) return cuda_fail(nullptr, fe, "composite layout upload");
+                return fail(nullptr, AMGDD_ERR_INVALID_ARG, "internal layout check failed: " + badf);
+            }
             S.fac_fma = 0;
             for (int p = 0; p < nsub; ++p)
                 S.fac_fma += F.work1[p] + (int64_t)(h->opt.n_fac - 1) * F.work[p];
@@ -521,13 +633,14 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             }
             std::vector<GlobalLevelDev> G;
             build_global_dev(h->H, G);
-            const std::string bad = validate_layouts(h->H, G, F);
+            const std::string bad = validate_global(h->H, G);
             if (!bad.empty()) {
                 delete h;
                 return fail(nullptr, AMGDD_ERR_INVALID_ARG, "internal layout check failed: " + bad);
             }
             // hybrid AMG-DD: composite grids of the hierarchy from level Lt down
             FacLayout Fs;
+            FacStream FSs;
             int32_t hyb_ns = 0;
             if (h->opt.hybrid_level > 0) {
                 // subdomains of level Lt: each C point keeps the subdomain of
@@ -551,17 +664,22 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
                 Composite Cs;
                 std::vector<int> etas(eta.begin() + Lt, eta.end());
                 build_composite(Hs, pl.data(), hyb_ns, etas, Cs, nth);
-                build_fac_layout(Hs, Cs, Fs, nth, false);
-                const std::string bad2 = validate_layouts(Hs, {}, Fs);
+                FSs.host = h->opt.host_only == 3;
+                FacSink sinks;
+                if (to_dev) sinks = [&](FacLayout &Lf, int p0, int pn) { return FSs.consume(Hs, Lf, p0, pn, st_); };
+                std::string bad2 = build_fac_layout(Hs, Cs, Fs, nth, false, sinks);
+                if (bad2.empty()) bad2 = to_dev ? validate_fac_totals(Fs) : validate_layouts(Hs, {}, Fs);
                 if (!bad2.empty()) {
+                    const cudaError_t fe = FSs.err;
                     delete h;
+                    if (fe != cudaSuccess) return cuda_fail(nullptr, fe, "hybrid layout upload");
                     return fail(nullptr, AMGDD_ERR_INVALID_ARG, "internal hybrid layout check failed: " + bad2);
                 }
                 const int nls = nlev - Lt;
                 h->hyb_off.assign((size_t)nls + 1, 0);
                 for (int l = 0; l < nls; ++l) h->hyb_off[l + 1] = h->hyb_off[l] + Hs.lv[l].A.rows;
             }
-            if (h->opt.host_only == 2) goto done;
+            if (h->opt.host_only >= 2) goto done;
             auto bail = [&](cudaError_t e, const char *what) {
                 amgdd_status s2 = cuda_fail(nullptr, e, what);
                 for (void *p : h->allocs) cudaFree(p);
@@ -607,14 +725,14 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             // composite-grid layout
             {
                 const char *what = "";
-                if ((e = upload_fac(h, F, nlev, nsub, h->level_off, h->opt.precision == 1, st_, h->fac, &what)) !=
+                if ((e = upload_fac(h, F, FS, nlev, nsub, h->level_off, h->opt.precision == 1, st_, h->fac, &what)) !=
                     cudaSuccess)
                     return bail(e, what);
             }
             if (hyb_ns > 0) {
                 const int nls = nlev - h->opt.hybrid_level;
                 const char *what = "";
-                if ((e = upload_fac(h, Fs, nls, hyb_ns, h->hyb_off, false, st_, h->fac_hyb, &what)) != cudaSuccess)
+                if ((e = upload_fac(h, Fs, FSs, nls, hyb_ns, h->hyb_off, false, st_, h->fac_hyb, &what)) != cudaSuccess)
                     return bail(e, what);
                 if ((e = alloc(h, (size_t)h->hyb_off.back(), &h->r_hyb)) != cudaSuccess)
                     return bail(e, "alloc hybrid residual");

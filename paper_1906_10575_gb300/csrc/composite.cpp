@@ -281,9 +281,9 @@ void emit_view(RowList &rl, int32_t first_row, int32_t rows_total_level, FacView
     for (int32_t s = 0; s * 32 < n; ++s) {
         int64_t width = 0;
         for (int32_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) width = std::max(width, rl.ptr[r + 1] - rl.ptr[r]);
-        const int64_t base = (int64_t)V.size();
+        const int64_t base = (int64_t)V.size();   // held entries; soff is absolute
         const size_t end = (size_t)(base + 32 * width);
-        V.soff.push_back(base);
+        V.soff.push_back(V.base + base);
         if (V.c16) V.col16.resize(end, 0); else V.col32.resize(end, 0);
         if (V.v32) V.val32.resize(end, 0.0f); else V.val64.resize(end, 0.0);
         for (int32_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) {
@@ -295,7 +295,7 @@ void emit_view(RowList &rl, int32_t first_row, int32_t rows_total_level, FacView
             }
         }
     }
-    V.soff.push_back((int64_t)V.size());
+    V.soff.push_back(V.total());
     for (int32_t r = 0; r < rows_total_level; ++r) {
         const int32_t v = r - first_row;
         V.rlen.push_back(v >= 0 && v < n ? (uint16_t)(rl.ptr[v + 1] - rl.ptr[v]) : (uint16_t)0);
@@ -306,7 +306,8 @@ void emit_view(RowList &rl, int32_t first_row, int32_t rows_total_level, FacView
 
 }  // namespace
 
-void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads, bool fp32)
+std::string build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int nthreads, bool fp32,
+                             const FacSink &sink)
 {
     const int L = H.L();
     const int nlev = L + 1;
@@ -496,15 +497,15 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
             F.lvAFc[l] += G.AFc[l].ptr.back();
             F.lvP[l] += G.P[l].ptr.back();
             F.lvR[l] += G.R[l].ptr.back();
-            d.sA = (int64_t)F.A.soff.size();
+            d.sA = F.A.sbase + (int64_t)F.A.soff.size();
             emit_view(G.A[l], 0, nbar, F.A);
-            d.sAt = (int64_t)F.At.soff.size();
+            d.sAt = F.At.sbase + (int64_t)F.At.soff.size();
             emit_view(G.At[l], 0, nbar, F.At);
-            d.sAFc = (int64_t)F.AFc.soff.size();
+            d.sAFc = F.AFc.sbase + (int64_t)F.AFc.soff.size();
             emit_view(G.AFc[l], d.nC, nbar, F.AFc);
-            d.sP = (int64_t)F.P.soff.size();
+            d.sP = F.P.sbase + (int64_t)F.P.soff.size();
             emit_view(G.P[l], 0, nbar, F.P);
-            d.sR = (int64_t)F.R.soff.size();
+            d.sR = F.R.sbase + (int64_t)F.R.soff.size();
             emit_view(G.R[l], 0, nbar, F.R);
             row0 += nbar;
         }
@@ -514,12 +515,18 @@ void build_fac_layout(const Hierarchy &H, const Composite &C, FacLayout &F, int 
         F.work1[p] = G.work1;
         G = GridBuild();
     }
+    F.rows_total = row0;
+    if (sink) {
+        const std::string e = sink(F, p0, pn);
+        if (!e.empty()) return e;
+    }
     }
     F.rows_total = row0;
     F.order.resize((size_t)nsub);
     std::iota(F.order.begin(), F.order.end(), 0);
     std::stable_sort(F.order.begin(), F.order.end(),
                      [&](int32_t a, int32_t b) { return F.work[a] > F.work[b]; });
+    return "";
 }
 
 }  // namespace amgdd
@@ -529,16 +536,19 @@ namespace amgdd {
 namespace {
 
 // Checks one SELL block: slices cover exactly `rows` rows, every row length
-// fits its slice width, and every stored column lies in [0, ncols).
+// fits its slice width, and every stored column lies in [0, ncols). Slice
+// offsets are absolute; `lo` is the first entry still held and `hi` one past
+// the last, and colat takes an absolute entry index.
 template <class ColAt>
 std::string check_sell_g(const std::vector<int64_t> &soff, int64_t s0, const std::vector<uint16_t> &rlen, int64_t r0,
-                         int64_t rows, size_t ncol_entries, ColAt colat, int64_t ncols, const char *what)
+                         int64_t rows, int64_t lo, int64_t hi, ColAt colat, int64_t ncols, const char *what)
 {
     const int64_t nsl = (rows + 31) / 32;
+    if (s0 < 0 || r0 < 0) return std::string(what) + ": slices or rows no longer held";
     if (s0 + nsl >= (int64_t)soff.size() + (rows == 0 ? 1 : 0)) return std::string(what) + ": slice table too short";
     for (int64_t q = 0; q < nsl; ++q) {
         const int64_t a = soff[s0 + q], b = soff[s0 + q + 1];
-        if (a < 0 || b < a || b > (int64_t)ncol_entries || (b - a) % 32) return std::string(what) + ": bad slice offsets";
+        if (a < lo || b < a || b > hi || (b - a) % 32) return std::string(what) + ": bad slice offsets";
         const int64_t width = (b - a) / 32;
         for (int lane = 0; lane < 32; ++lane) {
             const int64_t r = q * 32 + lane;
@@ -547,7 +557,7 @@ std::string check_sell_g(const std::vector<int64_t> &soff, int64_t s0, const std
             const int64_t len = rlen[r0 + r];
             if (len > width) return std::string(what) + ": row longer than its slice";
             for (int64_t k = 0; k < len; ++k) {
-                const int32_t c = colat((size_t)(a + 32 * k + lane));
+                const int32_t c = colat(a + 32 * k + lane);
                 if (c < 0 || c >= ncols) return std::string(what) + ": column out of range";
             }
         }
@@ -558,18 +568,20 @@ std::string check_sell_g(const std::vector<int64_t> &soff, int64_t s0, const std
 std::string check_view(const FacView &V, int64_t s0, int64_t r0, int64_t rows, int64_t ncols, const char *what)
 {
     if ((V.v32 ? V.val32.size() : V.val64.size()) != V.size()) return std::string(what) + ": value array size";
-    return check_sell_g(V.soff, s0, V.rlen, r0, rows, V.size(), [&](size_t i) { return V.col(i); }, ncols, what);
+    return check_sell_g(V.soff, s0 - V.sbase, V.rlen, r0 - V.rbase, rows, V.base, V.total(),
+                        [&](int64_t i) { return V.col((size_t)(i - V.base)); }, ncols, what);
 }
 
 std::string check_sell(const std::vector<int64_t> &soff, int64_t s0, const std::vector<uint16_t> &rlen, int64_t r0,
                        int64_t rows, const std::vector<int32_t> &col, int64_t ncols, const char *what)
 {
-    return check_sell_g(soff, s0, rlen, r0, rows, col.size(), [&](size_t i) { return col[i]; }, ncols, what);
+    return check_sell_g(soff, s0, rlen, r0, rows, 0, (int64_t)col.size(), [&](int64_t i) { return col[(size_t)i]; },
+                        ncols, what);
 }
 
 }  // namespace
 
-std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDev> &G, const FacLayout &F)
+std::string validate_global(const Hierarchy &H, const std::vector<GlobalLevelDev> &G)
 {
     const int L = H.L();
     std::string e;
@@ -586,16 +598,22 @@ std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDe
             if (g.P.rows != n || g.R.rows != nc) return "global P/R row counts";
         }
     }
-    if (F.nsub == 0) return "";
-    for (const FacView *V : {&F.A, &F.At, &F.AFc, &F.P, &F.R})
-        if ((int64_t)V->rlen.size() != F.rows_total) return "view row-length table size";
-    for (int p = 0; p < F.nsub; ++p) {
+    return "";
+}
+
+std::string validate_fac_grids(const Hierarchy &H, const FacLayout &F, int p0, int pn)
+{
+    const int L = H.L();
+    std::string e;
+    for (int p = p0; p < p0 + pn; ++p) {
         for (int l = 0; l <= L; ++l) {
             const FacLevelDesc &d = F.desc[(size_t)p * F.nlev + l];
             if (d.nC < 0 || d.nC > d.nReal || d.nReal > d.nBar) return "composite counts";
-            if (d.row0 < 0 || d.row0 + d.nBar > F.rows_total) return "composite row range";
+            if (d.row0 < F.row_base || d.row0 + d.nBar > F.rows_total ||
+                d.row0 + d.nBar - F.row_base > (int64_t)F.gmap.size())
+                return "composite row range";
             for (int32_t r = 0; r < d.nBar; ++r) {
-                const int32_t gi = F.gmap[d.row0 + r];
+                const int32_t gi = F.gmap[(size_t)(d.row0 - F.row_base + r)];
                 if (gi < 0 || gi >= H.lv[l].A.rows) return "composite map out of range";
             }
             const int64_t nup = l < L ? F.desc[(size_t)p * F.nlev + l + 1].nBar : 0;
@@ -612,12 +630,30 @@ std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDe
         for (int64_t k = F.owned0[p]; k < F.owned0[p + 1]; ++k)
             if (F.owned[k] < 0 || F.owned[k] >= d0.nReal) return "owned index out of range";
     }
+    return "";
+}
+
+std::string validate_fac_totals(const FacLayout &F)
+{
+    for (const FacView *V : {&F.A, &F.At, &F.AFc, &F.P, &F.R})
+        if (V->rbase + (int64_t)V->rlen.size() != F.rows_total) return "view row-length table size";
+    if (F.row_base + (int64_t)F.gmap.size() != F.rows_total || F.row_base + (int64_t)F.l1inv.size() != F.rows_total)
+        return "composite row count";
     std::vector<uint8_t> seen((size_t)F.nsub, 0);
+    if (F.order.size() != (size_t)F.nsub) return "grid order is not a permutation";
     for (int32_t p : F.order) {
         if (p < 0 || p >= F.nsub || seen[p]) return "grid order is not a permutation";
         seen[p] = 1;
     }
     return "";
+}
+
+std::string validate_layouts(const Hierarchy &H, const std::vector<GlobalLevelDev> &G, const FacLayout &F)
+{
+    std::string e = validate_global(H, G);
+    if (!e.empty() || F.nsub == 0) return e;
+    if (!(e = validate_fac_totals(F)).empty()) return e;
+    return validate_fac_grids(H, F, 0, F.nsub);
 }
 
 }  // namespace amgdd

@@ -36,7 +36,7 @@ def _loss_and_grad(kappa_np, b_np, xt_np, box, tol):
     x = diffusion_solve(kappa, b, box=box, padding=2, tol=tol)
     loss = 0.5 * torch.sum((x - xt) ** 2)
     loss.backward()
-    return float(loss), kappa.grad.cpu().numpy().reshape(-1), b.grad.cpu().numpy(), x.detach().cpu().numpy()
+    return float(loss.detach()), kappa.grad.cpu().numpy().reshape(-1), b.grad.cpu().numpy(), x.detach().cpu().numpy()
 
 
 def _loss(kappa_np, b_np, xt_np, box, tol):

@@ -67,3 +67,25 @@ def test_box_partition_and_rhs_seed():
     b0 = I.uniform_rhs(1000, 0)
     assert np.array_equal(b0, np.random.default_rng(0).uniform(-1, 1, 1000))
     assert b0.min() >= -1 and b0.max() <= 1
+
+
+def test_batched_poisson_is_block_diagonal():
+    """The batch is the direct sum of the single-system Poisson matrices, each
+    partitioned into its own boxes (uneven at the far ends), in draw order."""
+    rp, ci, v, part, nsub, B, picks, offs = I.batched_poisson(5, edges=(8, 12, 20), box=8, nrhs=4, seed=11)
+    assert len(picks) == 5 and set(picks) <= {8, 12, 20}
+    assert B.shape == (offs[-1], 4) and np.all(np.abs(B) <= 1.0)
+    sub0 = 0
+    for k, e in enumerate(picks):
+        a, b = offs[k], offs[k + 1]
+        assert b - a == e ** 3
+        r1, c1, v1 = I.poisson3d(e, e, e)
+        blk = rp[a:b + 1] - rp[a]
+        assert np.array_equal(blk, r1)
+        assert np.array_equal(ci[rp[a]:rp[b]] - a, c1) and np.array_equal(v[rp[a]:rp[b]], v1)
+        p1, n1 = I.box_partition((e, e, e), (8, 8, 8))
+        assert np.array_equal(part[a:b] - sub0, p1)
+        sub0 += n1
+    assert nsub == sub0 == part.max() + 1
+    again = I.batched_poisson(5, edges=(8, 12, 20), box=8, nrhs=4, seed=11)
+    assert np.array_equal(again[5], B) and again[6] == picks

@@ -221,6 +221,16 @@ WORKLOADS = {
     # 3D 7-point Poisson 128^3, 8x8x8 boxes of 16^3, padding 2 on every level
     "poisson3d_128": dict(shape=(128, 128, 128), box=(16, 16, 16), padding=2,
                           n_fac=2),
+    # 3D 7-point -div(kappa grad u) on 256^3, kappa constant on 8^3 blocks of
+    # 32^3 nodes, i.i.d. {1, 1e3} with p = 1/2; 4096 boxes of 16^3, padding 2;
+    # FP32 AlgFAC inside FP64 refinement
+    "kappa3d_256": dict(shape=(256, 256, 256), box=(16, 16, 16), padding=2, n_fac=2,
+                        kappa_blocks=8, precision=1),
+    # 64 independent 3D 7-point Poisson systems, edges i.i.d. from
+    # {32, 48, 64, 80, 96}, boxes of 16^3, 4 right-hand sides each, FP32
+    # AlgFAC inside FP64 refinement
+    "batched_64": dict(nsys=64, edges=(32, 48, 64, 80, 96), box=(16, 16, 16), padding=2, n_fac=2,
+                       nrhs=4, precision=1),
 }
 
 
@@ -231,8 +241,17 @@ def workload(name: str, seed: int = 0, shape=None, box=None):
         w["shape"] = tuple(shape)
     if box is not None:
         w["box"] = tuple(box)
+    if "nsys" in w:
+        rp, ci, v, part, nsub, B, picks, offs = batched_poisson(
+            w["nsys"], edges=w["edges"], box=w["box"][0], nrhs=w["nrhs"], seed=seed)
+        return dict(rowptr=rp, col=ci, val=v, part=part, nsub=nsub, B=B, b=np.ascontiguousarray(B[:, 0]),
+                    padding=w["padding"], n_fac=w["n_fac"], edges=picks, offsets=offs, nrhs=w["nrhs"],
+                    precision=w["precision"], box=w["box"], name=name, seed=seed)
     shape = w["shape"]
-    if len(shape) == 2:
+    if "kappa_blocks" in w:
+        kappa = checkerboard_kappa(shape[0], w["kappa_blocks"], seed)
+        rp, ci, v = diffusion3d(kappa)
+    elif len(shape) == 2:
         rp, ci, v = poisson2d(*shape)
     else:
         rp, ci, v = poisson3d(*shape)
@@ -240,4 +259,4 @@ def workload(name: str, seed: int = 0, shape=None, box=None):
     b = uniform_rhs(int(np.prod(shape)), seed)
     return dict(rowptr=rp, col=ci, val=v, part=part, nsub=nsub, b=b,
                 padding=w["padding"], n_fac=w["n_fac"], shape=shape,
-                box=w["box"], name=name, seed=seed)
+                box=w["box"], name=name, seed=seed, precision=w.get("precision", 0))

@@ -253,6 +253,147 @@ def cpu_baseline(w, iters):
                       "threads), scaled by %d iterations" % (w["nsub"], t_iter, cores, iters)}
 
 
+def _ev_ms(stream, fn, k=1):
+    """Mean CUDA-event time of k calls of fn on `stream` (ms)."""
+    import torch
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(k):
+        fn()
+    a1.record(stream)
+    a1.synchronize()
+    return a0.elapsed_time(a1) / k
+
+
+def run_extra(args, name, stream, dist, local):
+    """The two larger configurations, one JSON line each (not the headline):
+
+    kappa3d_256 -- 256^3 variable-coefficient diffusion, 4096 composite grids,
+      FP32 AlgFAC inside FP64 refinement; AMG-DD against the FP64 V-cycle on
+      the same hierarchy, and the final error against the FP64 AMG-DD
+      solution (whose iterates equal the CPU oracle's bit for bit).
+    batched_64 -- 64 independent Poisson systems as one block-diagonal matrix,
+      4 right-hand sides, FP32 AlgFAC inside FP64 refinement, one
+      several-column FAC launch per iteration in a CUDA graph; against four
+      single-column FP64 V-cycle solves on the same hierarchy."""
+    import torch
+    from paper_1906_10575_gb300 import Solver, capi
+
+    w = I.workload(name, seed=0)
+    n = int(len(w["rowptr"]) - 1)
+    hbm, peak_kind = _peaks()
+    multi = "nsys" in I.WORKLOADS[name]
+    t0 = time.perf_counter()
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+               precision=1, schedule=args.schedule, stream=stream, max_coarse=16 * (64 if multi else 1))
+    setup_s = time.perf_counter() - t0
+    st = s.stats
+    nrhs = w["nrhs"] if multi else 1
+    Bh = w["B"] if multi else w["b"][:, None]
+    B = torch.from_numpy(np.ascontiguousarray(Bh)).cuda()
+    X = torch.zeros_like(B)
+    solve = (lambda: s.solve_multi(B, X, tol=TOL, max_iter=200, stream=stream)) if multi else \
+        (lambda: s.solve(B[:, 0], X[:, 0], tol=TOL, max_iter=200, stream=stream))
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            X.zero_()
+            solve()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        times = []
+        for _ in range(args.steps):
+            X.zero_()
+            torch.cuda.synchronize()
+            info = {}
+            times.append(_ev_ms(stream, lambda: info.update(solve())))
+        clocks = clk.stop()
+        # the FAC launch alone, from the restricted residuals of B (x = 0)
+        off = int(s.offsets[-1])
+        Rcols = []
+        for j in range(nrhs):
+            r = torch.zeros(off, dtype=torch.float64, device="cuda")
+            capi.amgdd_residual(s.h, B[:, j].contiguous(), torch.zeros(n, dtype=torch.float64, device="cuda"),
+                                r[:n], stream)
+            capi.amgdd_restrict(s.h, r, stream)
+            Rcols.append(r)
+        Xf = torch.zeros_like(X)
+        if multi:
+            Rm = torch.stack(Rcols, 1).contiguous()
+            fac = lambda: capi.amgdd_fac_multi(s.h, Rm, Xf, stream)  # noqa: E731
+        else:
+            xf = torch.zeros(n, dtype=torch.float64, device="cuda")
+            fac = lambda: capi.amgdd_fac(s.h, Rcols[0], xf, stream)  # noqa: E731
+        fac()
+        fac_ms = _ev_ms(stream, fac, 3)
+        Xmix = X.clone()
+        # FP64 V-cycle on the same hierarchy, column by column
+        xv = torch.zeros(n, dtype=torch.float64, device="cuda")
+        v_ms, v_it = 0.0, []
+        for j in range(nrhs):
+            bj = B[:, j].contiguous()
+            xv.zero_()
+            s.vcycle_solve(bj, xv, tol=TOL, max_iter=200, stream=stream)
+            xv.zero_()
+            torch.cuda.synchronize()
+            iv = {}
+            v_ms += _ev_ms(stream, lambda: iv.update(s.vcycle_solve(bj, xv, tol=TOL, max_iter=200, stream=stream)))
+            v_it.append(iv["iterations"])
+    s.close()
+    ms = statistics.median(times)
+    ms, v_ms = max_over_ranks([ms, v_ms], dist)
+    fac_b = algorithmic_fac_bytes(st, w["n_fac"], sv=4.0)
+    # several columns: the operator once, the vector touches once per column
+    if multi:
+        L = st.num_levels - 1
+        vec = sum(4.0 * 8 * (st.comp_real[l] + st.comp_ghost[l]) for l in range(L)) * w["n_fac"]
+        fac_b = fac_b + (nrhs - 1) * vec
+    fac_gbs = fac_b / (fac_ms * 1e-3) / 1e9
+    err = None
+    if not multi and not args.no_fp64_check:
+        # FP64 AMG-DD on the same problem: reference solution for the error
+        s64 = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                     stream=stream)
+        x64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            i64 = s64.solve(B[:, 0], x64, tol=TOL, max_iter=200, stream=stream)
+            torch.cuda.synchronize()
+        err = {"rel_error_vs_fp64_amgdd": float(torch.linalg.vector_norm(Xmix[:, 0] - x64)
+                                                / torch.linalg.vector_norm(x64)),
+               "fp64_iterations": i64["iterations"], "fp64_final_relres": i64["final_relres"]}
+        s64.close()
+    it = info["iterations"]
+    if multi:
+        desc = ("%d independent 3D 7-point Poisson systems (edges %s drawn from {32,48,64,80,96}, N=%d total), "
+                "boxes of 16^3 (%d subdomains), padding 2, %d right-hand sides U[-1,1], "
+                "FP32 AlgFAC / FP64 refinement" % (len(w["edges"]), ",".join(map(str, sorted(set(w["edges"])))),
+                                                     n, w["nsub"], nrhs))
+    else:
+        desc = ("3D 7-point diffusion 256^3 (N=%d), kappa on 8^3 blocks of 32^3 i.i.d. {1,1e3}, %d subdomains "
+                "of 16^3, padding 2, FP32 AlgFAC / FP64 refinement, b~U[-1,1] seed 0" % (n, w["nsub"]))
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "dtype": "f32 AlgFAC / f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": desc, "n": n, "nnz": int(len(w["col"])), "nsub": int(w["nsub"]), "nrhs": nrhs,
+                   "l2_policy": "inputs larger than L2"},
+        "iterations": it, "final_relres": info["final_relres"],
+        "vcycle_fp64": {"ms_all_columns": round(v_ms, 3), "iterations": v_it},
+        "amgdd_over_vcycle_time": round(ms / v_ms, 3),
+        "fac": {"kernel": "k_fac_all_grids_r" if multi else "k_fac_all_grids", "ms_per_launch": round(fac_ms, 3),
+                "algorithmic_bytes": fac_b, "achieved_gbs": round(fac_gbs, 1), "peak_gbs": hbm,
+                "hbm_frac": round(fac_gbs / hbm, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+        "composite_overhead": round(st.composite_overhead, 3), "levels": st.num_levels,
+        "coarsest": int(st.n[st.num_levels - 1]), "setup_s": round(setup_s, 1),
+        "device_gb": round(st.device_bytes / 1e9, 2),
+        "gpu_launches_per_step": int(info["kernel_launches"]),
+        "clocks": clocks, "fp64_check": err,
+    }
+    if multi:
+        line["edges"] = list(map(int, w["edges"]))
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -268,10 +409,25 @@ def main():
     ap.add_argument("--n", type=int, default=128,
                     help="grid edge (default 128, the benchmark workload; smaller edges "
                          "are for profiling captures only)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "kappa3d_256", "batched_64"],
+                    help="poisson3d_128 (default, the headline) or one of the two larger "
+                         "mixed-precision configurations, printed as a line of their own")
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="kappa3d_256: skip the FP64 AMG-DD solve used for the final error")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload != WORKLOAD:
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm runs the headline "
+                                  "workload only; %s is measured on the GPU path" % args.workload}))
+            return
+        import torch
+        torch.cuda.set_device(local)
+        run_extra(args, args.workload, torch.cuda.Stream(), None, local)
+        return
     w = I.workload(WORKLOAD, seed=0, shape=(args.n,) * 3)
 
     if args.impl == "reference":

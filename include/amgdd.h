@@ -249,6 +249,13 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
 /* One AMG-DD iteration (Algorithm 2) for all columns. */
 amgdd_status amgdd_iterate_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, void *stream);
 
+/* Algorithm 2, steps 3-5 for all columns in one launch (amgdd_fac for nrhs
+ * columns). R_all: DEVICE, the restricted residuals of every level, level l
+ * at row offset sum_{k<l} n_k, each level stored row by row with its nrhs
+ * values side by side (R_all[(off_l + i) * nrhs + j]); X: DEVICE, n x nrhs
+ * row by row, updated in place. */
+amgdd_status amgdd_fac_multi(amgdd_handle h, const double *R_all, double *X, int32_t nrhs, void *stream);
+
 /* AMG-DD solver for all columns: iterates until every column satisfies
  * ||b_j - A x_j|| / ||b_j|| <= tol (or max_iter). info->history (HOST, may be
  * NULL) receives nrhs * (max_iter + 1) doubles, column j's history at

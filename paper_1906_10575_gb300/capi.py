@@ -61,7 +61,7 @@ EXPORTS = [
     "amgdd_last_error", "amgdd_get_stats", "amgdd_get_maps", "amgdd_get_operator", "amgdd_get_cf",
     "amgdd_get_coarse_inverse", "amgdd_residual", "amgdd_restrict", "amgdd_fac",
     "amgdd_get_fac_state", "amgdd_iterate", "amgdd_solve", "amg_vcycle", "amg_vcycle_solve",
-    "amgdd_residual_csr_noalloc", "amgdd_iterate_multi", "amgdd_solve_multi",
+    "amgdd_residual_csr_noalloc", "amgdd_iterate_multi", "amgdd_fac_multi", "amgdd_solve_multi",
     "amg_hybrid_cycle", "amg_hybrid_solve", "amgdd_kappa_grad_3d",
 ]
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "amg_vcycle_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
         "amgdd_residual_csr_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
         "amgdd_iterate_multi": [vp, vp, vp, i32, vp],
+        "amgdd_fac_multi": [vp, vp, vp, i32, vp],
         "amg_hybrid_cycle": [vp, vp, vp, vp],
         "amgdd_kappa_grad_3d": [i32, i32, i32, vp, vp, vp, vp, vp],
         "amg_hybrid_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
@@ -287,6 +288,12 @@ def amgdd_residual_csr_noalloc(n, rowptr, col, val, b, x, r, nrm2, stream=None):
 def amgdd_iterate_multi(h, B, X, stream=None):
     """One AMG-DD iteration for every column of B / X (device, shape (n, nrhs))."""
     _check(load().amgdd_iterate_multi(h, _ptr(B), _ptr(X), int(B.shape[1]), _stream(stream)), h)
+
+
+def amgdd_fac_multi(h, R_all, X, stream=None):
+    """FAC step for every column: R_all (device, shape (sum_l n_l, nrhs)) holds
+    the restricted residuals of all levels; X (device, (n, nrhs)) is updated."""
+    _check(load().amgdd_fac_multi(h, _ptr(R_all), _ptr(X), int(X.shape[1]), _stream(stream)), h)
 
 
 def amgdd_solve_multi(h, B, X, tol=1e-8, max_iter=200, stream=None, raise_on_noconv=True):

@@ -1175,6 +1175,24 @@ amgdd_status amgdd_iterate_multi(amgdd_handle h, const double *B, double *X, int
     return iterate_multi(h, *m, B, X, true, (cudaStream_t)stream);
 }
 
+amgdd_status amgdd_fac_multi(amgdd_handle h, const double *R_all, double *X, int32_t nrhs, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (!R_all || !X || (nrhs != 2 && nrhs != 4)) return fail(h, AMGDD_ERR_INVALID_ARG, "nrhs must be 2 or 4");
+    amgdd_handle_s::Multi *m;
+    if ((s = multi_space(h, nrhs, &m)) != AMGDD_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    FacParams P = h->fac;
+    P.u = m->ws[0]; P.f = m->ws[1]; P.t = m->ws[2]; P.s = m->ws[3]; P.w = m->ws[4]; P.d = m->ws[5];
+    P.r_all = R_all;
+    P.x = X;
+    CK(launch_fac_multi(P, P.nsub, nrhs, st), "FAC kernel");
+    h->launches += 1;
+    return AMGDD_OK;
+}
+
 amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, double tol, int32_t max_iter,
                                void *stream, amgdd_solve_info *info)
 {

@@ -51,6 +51,9 @@ def _case(name):
         rp, ci, v = I.poisson2d(40, 40)
         part, nsub = I.box_partition((40, 40), (10, 10))
         return rp, ci, v, part, nsub, 0, I.uniform_rhs(1600, 5)
+    if name == "batch3":     # three independent systems, block diagonal, uneven boxes
+        rp, ci, v, part, nsub, B, picks, offs = I.batched_poisson(3, edges=(12, 16, 20), box=8, nrhs=1, seed=5)
+        return rp, ci, v, part, nsub, 2, B[:, 0].copy()
     if name == "single_level":  # n <= max_coarse: only the coarsest solve
         rp, ci, v = I.poisson2d(4, 3)
         part, nsub = I.box_partition((4, 3), (2, 3))
@@ -230,7 +233,7 @@ def test_mixed_precision_fac_and_solve_bit_exact(case):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("nrhs", [2, 4])
-@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d"])
+@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d", "batch3"])
 def test_multi_rhs_columns_equal_single_column_solves(case, nrhs, precision):
     """Columns solved together follow exactly the single-column arithmetic:
     each column's iterate after k iterations equals the oracle's k
@@ -259,6 +262,29 @@ def test_multi_rhs_columns_equal_single_column_solves(case, nrhs, precision):
         _, ho = o.amgdd_solve(Bh[:, j], 2, tol=0.0, maxit=k, mixed=bool(precision))
         assert np.allclose(info["history"][j], ho, rtol=1e-12, atol=0), j
     assert info["converged"] and info["history"][:, -1].max() <= 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["batch3", "kappa3d"])
+def test_fac_multi_equals_oracle_corrections(case, precision):
+    """The several-column FAC launch alone: from the restricted residuals of
+    b_j (the residual of x = 0), column j of the correction equals the
+    oracle's AMG-DD iteration on b_j from zero."""
+    rp, ci, v, part, nsub, pad, _ = _case(case)
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, precision=precision)
+    n = s.n
+    Bh = np.stack([I.uniform_rhs(n, 20 + j) for j in range(4)], axis=1)
+    Rh = np.stack([np.concatenate(o.restrict_all(Bh[:, j])) for j in range(4)], axis=1)
+    assert Rh.shape[0] == int(s.offsets[-1])
+    R = torch.from_numpy(np.ascontiguousarray(Rh)).cuda()
+    X = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    capi.amgdd_fac_multi(s.h, R, X)
+    Xh = _host(X)
+    step = o.amgdd_iteration32 if precision else (lambda b, x, nf: o.amgdd_iteration(b, x, nf))
+    for j in range(4):
+        assert np.array_equal(Xh[:, j], step(Bh[:, j], np.zeros(n), 2)), j
     s.close()
 
 

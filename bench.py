@@ -295,6 +295,10 @@ def run_extra(args, name, stream, dist, local):
     X = torch.zeros_like(B)
     solve = (lambda: s.solve_multi(B, X, tol=TOL, max_iter=200, stream=stream)) if multi else \
         (lambda: s.solve(B[:, 0], X[:, 0], tol=TOL, max_iter=200, stream=stream))
+    tune = None
+    if not args.no_autotune:
+        best, tms = capi.amgdd_autotune(s.h, nrhs, reps=2, stream=stream)
+        tune = {"best_candidate": best, "ms_per_candidate": [round(float(t), 3) for t in tms]}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             X.zero_()
@@ -386,8 +390,9 @@ def run_extra(args, name, stream, dist, local):
         "composite_overhead": round(st.composite_overhead, 3), "levels": st.num_levels,
         "coarsest": int(st.n[st.num_levels - 1]), "setup_s": round(setup_s, 1),
         "device_gb": round(st.device_bytes / 1e9, 2),
+        "host_peak_gb": round(__import__("resource").getrusage(__import__("resource").RUSAGE_SELF).ru_maxrss / 1e6, 1),
         "gpu_launches_per_step": int(info["kernel_launches"]),
-        "clocks": clocks, "fp64_check": err,
+        "clocks": clocks, "fp64_check": err, "autotune": tune,
     }
     if multi:
         line["edges"] = list(map(int, w["edges"]))
@@ -412,6 +417,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "kappa3d_256", "batched_64"],
                     help="poisson3d_128 (default, the headline) or one of the two larger "
                          "mixed-precision configurations, printed as a line of their own")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="larger workloads: keep the default FAC kernel instead of timing every candidate")
+    ap.add_argument("--autotune", action="store_true",
+                    help="headline workload: time every FAC kernel candidate and keep the fastest")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="kappa3d_256: skip the FP64 AMG-DD solve used for the final error")
     args = ap.parse_args()
@@ -449,6 +458,10 @@ def main():
     st = s.stats
     b = torch.from_numpy(w["b"]).cuda()
     x = torch.zeros_like(b)
+    tune = None
+    if args.autotune:
+        best, tms = capi.amgdd_autotune(s.h, 1, reps=2, stream=stream)
+        tune = {"best_candidate": best, "ms_per_candidate": [round(float(t), 3) for t in tms]}
 
     def barrier():
         if dist is not None:
@@ -663,6 +676,7 @@ def main():
         "e2e": {"value": round(ms_e2e, 3), "unit": "ms", "h2d_bytes_per_step": 8 * s.n,
                 "d2h_bytes_per_step": 8 * s.n},
         "clocks": clocks,
+        "autotune": tune,
         "mixed_precision": mixed,
         "multi_rhs": multi,
         "hybrid": hybrid,

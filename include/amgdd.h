@@ -264,6 +264,37 @@ amgdd_status amgdd_fac_multi(amgdd_handle h, const double *R_all, double *X, int
 amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32_t nrhs, double tol,
                                int32_t max_iter, void *stream, amgdd_solve_info *info);
 
+/* ---- FAC kernel choice -------------------------------------------------------
+ * The paper leaves the mapping of the composite-grid cycles onto hardware
+ * open; these calls choose among kernels that all compute the same values
+ * (every row product is the same ascending fma chain, so iterates do not
+ * depend on the choice). Candidates, numbered k = 0 .. AMGDD_FAC_CANDIDATES-1:
+ *   k = 0..8  : the single-column kernel with schedule k + 1 (amgdd_options
+ *               .schedule; one column only; FP32 composite grids: k = 0, 7);
+ *   k = 9..17 : the several-column kernel (one column is a width of 1),
+ *               variant k - 8: operator entries in flight per row (1, 2 or 4)
+ *               and resident blocks of 512 threads per SM (2, 3 or 4):
+ *               9: 1/2, 10: 2/2, 11: 2/3, 12: 4/2, 13: 1/4, 14: 2/4; and with
+ *               the operator entries 2 or 4 steps ahead prefetched into L2:
+ *               15: 2/4 (2 ahead), 16: 2/3 (2 ahead), 17: 2/4 (4 ahead).
+ * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
+#define AMGDD_FAC_CANDIDATES 18
+
+/* Uses candidate k for the FAC step of nrhs (1, 2 or 4) columns from now on.
+ * Returns AMGDD_ERR_INVALID_ARG when k does not apply (see above). Drops the
+ * handle's captured solver graphs (they are captured again when next used). */
+amgdd_status amgdd_set_fac_kernel(amgdd_handle h, int32_t nrhs, int32_t candidate);
+
+/* Autotuner: times one warm-up and `reps` FAC launches of every candidate
+ * that applies to nrhs (1, 2 or 4) columns on this handle's composite grids
+ * (zero restricted residuals, a scratch solution allocated and freed here),
+ * with CUDA events on `stream`, and keeps the fastest as amgdd_set_fac_kernel
+ * would. ms (HOST, may be NULL): AMGDD_FAC_CANDIDATES doubles, the mean
+ * milliseconds per launch, -1 where a candidate does not apply. best (may be
+ * NULL): the chosen candidate. Overwrites the FAC work space (what
+ * amgdd_get_fac_state reads) and the handle's residual buffers. */
+amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, double *ms, int32_t *best, void *stream);
+
 /* ---- adjoint: gradient with respect to diffusion coefficients -------------
  * The paper has no adjoint; this supports differentiating solves of the 3D
  * 7-point diffusion operator -div(kappa grad u) with node-wise kappa, face

@@ -19,7 +19,8 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
-CU_SOURCES = ["kernels.cu", "kernels_multi.cu", "adjoint.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels.cu", "kernels_multi.cu", "fac_multi_r1.cu", "fac_multi_r2.cu", "fac_multi_r4.cu",
+              "adjoint.cu", "noalloc.cu"]
 CXX_SOURCES = ["hierarchy.cpp", "composite.cpp", "capi.cpp"]
 
 

@@ -63,7 +63,10 @@ EXPORTS = [
     "amgdd_get_fac_state", "amgdd_iterate", "amgdd_solve", "amg_vcycle", "amg_vcycle_solve",
     "amgdd_residual_csr_noalloc", "amgdd_iterate_multi", "amgdd_fac_multi", "amgdd_solve_multi",
     "amg_hybrid_cycle", "amg_hybrid_solve", "amgdd_kappa_grad_3d",
+    "amgdd_set_fac_kernel", "amgdd_autotune",
 ]
+
+FAC_CANDIDATES = 18
 
 _lib = None
 
@@ -99,6 +102,8 @@ def load(path: str = LIB_PATH):
         "amgdd_residual_csr_noalloc": [i32, vp, vp, vp, vp, vp, vp, vp, vp],
         "amgdd_iterate_multi": [vp, vp, vp, i32, vp],
         "amgdd_fac_multi": [vp, vp, vp, i32, vp],
+        "amgdd_set_fac_kernel": [vp, i32, i32],
+        "amgdd_autotune": [vp, i32, i32, vp, C.POINTER(i32), vp],
         "amg_hybrid_cycle": [vp, vp, vp, vp],
         "amgdd_kappa_grad_3d": [i32, i32, i32, vp, vp, vp, vp, vp],
         "amg_hybrid_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
@@ -294,6 +299,20 @@ def amgdd_fac_multi(h, R_all, X, stream=None):
     """FAC step for every column: R_all (device, shape (sum_l n_l, nrhs)) holds
     the restricted residuals of all levels; X (device, (n, nrhs)) is updated."""
     _check(load().amgdd_fac_multi(h, _ptr(R_all), _ptr(X), int(X.shape[1]), _stream(stream)), h)
+
+
+def amgdd_set_fac_kernel(h, nrhs, candidate):
+    """FAC kernel candidate for nrhs columns (see amgdd_autotune)."""
+    _check(load().amgdd_set_fac_kernel(h, int(nrhs), int(candidate)), h)
+
+
+def amgdd_autotune(h, nrhs=1, reps=3, stream=None):
+    """Times every FAC kernel candidate for nrhs columns and keeps the fastest.
+    Returns (best candidate, array of ms per candidate, -1 where n/a)."""
+    ms = np.zeros(FAC_CANDIDATES, np.float64)
+    best = C.c_int32(-1)
+    _check(load().amgdd_autotune(h, int(nrhs), int(reps), ms.ctypes.data, C.byref(best), _stream(stream)), h)
+    return int(best.value), ms
 
 
 def amgdd_solve_multi(h, B, X, tol=1e-8, max_iter=200, stream=None, raise_on_noconv=True):

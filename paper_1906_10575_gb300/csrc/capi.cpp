@@ -79,6 +79,11 @@ struct amgdd_handle_s {
     FacParams fac_base{};
     // hybrid AMG-DD (Algorithm 3): composite grids of the hierarchy from level
     // hyb_level down, the residual of that level and its restrictions
+    // FAC kernel per column count (index 0: 1 column, 1: 2, 2: 4): for one
+    // column 0 selects the single-column kernel (schedule in fac.schedule),
+    // v >= 1 the several-column kernel's variant v; for 2 and 4 columns the
+    // several-column kernel's variant
+    int fac_variant[3] = {0, 1, 1};
     int hyb_level = -1;
     FacParams fac_hyb{};
     double *r_hyb = nullptr;
@@ -860,7 +865,8 @@ static amgdd_status fac(amgdd_handle h, const double *r_all, double *x, cudaStre
     FacParams P = h->fac;
     P.r_all = r_all;
     P.x = x;
-    CK(launch_fac_all_grids(P, P.nsub, h->threads, st), "FAC kernel");
+    if (h->fac_variant[0] > 0) CK(launch_fac_multi(P, P.nsub, 1, h->fac_variant[0], st), "FAC kernel");
+    else CK(launch_fac_all_grids(P, P.nsub, h->threads, st), "FAC kernel");
     h->launches += 1;
     return AMGDD_OK;
 }
@@ -1159,7 +1165,7 @@ static amgdd_status iterate_multi(amgdd_handle h, amgdd_handle_s::Multi &m, cons
     P.u = m.ws[0]; P.f = m.ws[1]; P.t = m.ws[2]; P.s = m.ws[3]; P.w = m.ws[4]; P.d = m.ws[5];
     P.r_all = m.r_all;
     P.x = X;
-    CK(launch_fac_multi(P, P.nsub, R, st), "FAC kernel");
+    CK(launch_fac_multi(P, P.nsub, R, h->fac_variant[R == 2 ? 1 : 2], st), "FAC kernel");
     h->launches += 1;
     return AMGDD_OK;
 }
@@ -1188,7 +1194,7 @@ amgdd_status amgdd_fac_multi(amgdd_handle h, const double *R_all, double *X, int
     P.u = m->ws[0]; P.f = m->ws[1]; P.t = m->ws[2]; P.s = m->ws[3]; P.w = m->ws[4]; P.d = m->ws[5];
     P.r_all = R_all;
     P.x = X;
-    CK(launch_fac_multi(P, P.nsub, nrhs, st), "FAC kernel");
+    CK(launch_fac_multi(P, P.nsub, nrhs, h->fac_variant[nrhs == 2 ? 1 : 2], st), "FAC kernel");
     h->launches += 1;
     return AMGDD_OK;
 }
@@ -1318,4 +1324,121 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
     return solve_loop(h, b, x, tol, max_iter, (cudaStream_t)stream, info, 2);
 }
 
+// ---------------------------------------------------------------------------
+// FAC kernel choice.
+
+// Candidate k of amgdd_autotune / amgdd_set_fac_kernel: k < 9 is the
+// single-column kernel with schedule k + 1 (one column only; FP32 composite
+// grids have schedules 1 and 8), k >= 9 the several-column kernel's variant
+// k - 8.
+static bool candidate_applies(amgdd_handle h, int nrhs, int k)
+{
+    if (k < 0 || k >= AMGDD_FAC_CANDIDATES) return false;
+    if (k < 9) return nrhs == 1 && (!h->fac.fp32 || k == 0 || k == 7);
+    return true;
+}
+
+static void drop_graphs(amgdd_handle h)
+{
+    for (auto &g : h->graph)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g = amgdd_handle_s::Graph();
+        }
+    for (auto &m : h->multi)
+        if (m.graph.exec) {
+            cudaGraphExecDestroy(m.graph.exec);
+            m.graph = amgdd_handle_s::Graph();
+        }
+}
+
+static void apply_candidate(amgdd_handle h, int nrhs, int k)
+{
+    const int idx = nrhs == 1 ? 0 : nrhs == 2 ? 1 : 2;
+    if (k < 9) {
+        h->fac_variant[0] = 0;
+        h->fac.schedule = k + 1;
+    } else {
+        h->fac_variant[idx] = k - 8;
+    }
+}
+
+amgdd_status amgdd_set_fac_kernel(amgdd_handle h, int32_t nrhs, int32_t candidate)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (nrhs != 1 && nrhs != 2 && nrhs != 4) return fail(h, AMGDD_ERR_INVALID_ARG, "nrhs must be 1, 2 or 4");
+    if (!candidate_applies(h, nrhs, candidate))
+        return fail(h, AMGDD_ERR_INVALID_ARG, "candidate does not apply to this handle and column count");
+    CK(cudaStreamSynchronize(h->last_stream), "sync");
+    drop_graphs(h);
+    apply_candidate(h, nrhs, candidate);
+    return AMGDD_OK;
+}
+
+amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, double *ms, int32_t *best, void *stream)
+{
+    amgdd_status s = require_device(h);
+    if (s != AMGDD_OK) return s;
+    if (nrhs != 1 && nrhs != 2 && nrhs != 4) return fail(h, AMGDD_ERR_INVALID_ARG, "nrhs must be 1, 2 or 4");
+    if (reps < 1) return fail(h, AMGDD_ERR_INVALID_ARG, "reps must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    // inputs: zero restricted residuals; output: a scratch x
+    FacParams P = h->fac;
+    double *r_all = h->r_all;
+    if (nrhs > 1) {
+        amgdd_handle_s::Multi *m;
+        if ((s = multi_space(h, nrhs, &m)) != AMGDD_OK) return s;
+        P.u = m->ws[0]; P.f = m->ws[1]; P.t = m->ws[2]; P.s = m->ws[3]; P.w = m->ws[4]; P.d = m->ws[5];
+        r_all = m->r_all;
+    }
+    CK(cudaMemsetAsync(r_all, 0, sizeof(double) * (size_t)h->level_off.back() * nrhs, st), "clear residuals");
+    double *xs = nullptr;
+    CK(cudaMalloc(&xs, sizeof(double) * (size_t)h->lev[0].n * nrhs), "alloc scratch x");
+    P.r_all = r_all;
+    P.x = xs;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int bk = -1;
+    double bms = 0.0;
+    for (int k = 0; k < AMGDD_FAC_CANDIDATES && e == cudaSuccess; ++k) {
+        if (ms) ms[k] = -1.0;
+        if (!candidate_applies(h, nrhs, k)) continue;
+        FacParams Q = P;
+        auto launch = [&]() -> cudaError_t {
+            if (k < 9) {
+                Q.schedule = k + 1;
+                return launch_fac_all_grids(Q, Q.nsub, h->threads, st);
+            }
+            return launch_fac_multi(Q, Q.nsub, nrhs, k - 8, st);
+        };
+        if ((e = launch()) != cudaSuccess) break;           // warm-up
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+        if (e != cudaSuccess) break;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+        const double per = (double)t / reps;
+        if (ms) ms[k] = per;
+        if (bk < 0 || per < bms) {
+            bk = k;
+            bms = per;
+        }
+        h->launches += 1 + reps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(xs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+    drop_graphs(h);
+    apply_candidate(h, nrhs, bk);
+    if (best) *best = bk;
+    return AMGDD_OK;
+}
+
 }  // extern "C"
+

@@ -1,0 +1,363 @@
+// Composite-grid FAC kernel for several right-hand sides at once (R = 1, 2
+// or 4): every vector is stored row by row with its R values side by side
+// (v[i * R + j]), and one load of an operator entry feeds R independent fma
+// chains. Column j's chain is exactly the single-right-hand-side chain (same
+// entries, same ascending order), so each column reproduces the
+// one-at-a-time result bit for bit. Instantiated per R in fac_multi_r*.cu.
+#pragma once
+
+#include <cstdint>
+
+#include "fac_device.cuh"
+#include "kernels.cuh"
+
+namespace amgdd {
+namespace dev {
+
+template <class T, int R>
+struct VecR {
+    T v[R];
+};
+
+// R consecutive values of the gathered vector (16- or 32-byte aligned groups
+// are loaded as vectors).
+template <class T, int R>
+__device__ __forceinline__ VecR<T, R> load_r(const T *__restrict__ p)
+{
+    VecR<T, R> o;
+    if constexpr (sizeof(T) == 4 && R == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        o.v[0] = q.x; o.v[1] = q.y; o.v[2] = q.z; o.v[3] = q.w;
+    } else if constexpr (sizeof(T) == 8 && R == 2) {
+        const double2 q = *reinterpret_cast<const double2 *>(p);
+        o.v[0] = q.x; o.v[1] = q.y;
+    } else if constexpr (sizeof(T) == 8 && R == 4) {
+        const double2 q0 = reinterpret_cast<const double2 *>(p)[0];
+        const double2 q1 = reinterpret_cast<const double2 *>(p)[1];
+        o.v[0] = q0.x; o.v[1] = q0.y; o.v[2] = q1.x; o.v[3] = q1.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) o.v[j] = p[j];
+    }
+    return o;
+}
+
+// Hint that the line holding p is wanted soon: fetched into L2, no register
+// is held and nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// s_j = sum_k a_k x[c_k * R + j] for the lane's row, one fma chain per column.
+// UNR entries are loaded before any of them is used (UNR operator loads and
+// UNR gathers in flight per lane); the fmas stay in ascending entry order.
+// PF > 0: each step first asks L2 for the operator entries PF steps ahead, so
+// their loads find them there instead of in HBM (entries past the row's
+// length are not touched).
+template <class CI, class T, int R, int UNR, int PF = 0, class SV>
+__device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint16_t *rlen, const CI *col,
+                                                 const SV *val, int64_t slice, int lane, int64_t row,
+                                                 const T *__restrict__ x)
+{
+    const int64_t base = __ldg(soff + slice) + lane;
+    const int len = __ldg(rlen + row);
+    VecR<T, R> s;
+#pragma unroll
+    for (int j = 0; j < R; ++j) s.v[j] = T(0);
+    int k = 0;
+    if constexpr (PF > 0) {
+#pragma unroll 1
+        for (; k + UNR <= len; k += UNR) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int kp = k + PF * UNR + u;
+                if (kp < len) {
+                    prefetch_l2(col + base + 32 * kp);
+                    prefetch_l2(val + base + 32 * kp);
+                }
+            }
+            int c[UNR];
+            T a[UNR];
+            VecR<T, R> xv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) c[u] = ld_op<true>(col + base + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<true>(val + base + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x + (int64_t)c[u] * R);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+#pragma unroll
+                for (int j = 0; j < R; ++j) s.v[j] = fma(a[u], xv[u].v[j], s.v[j]);
+        }
+    }
+    if constexpr (UNR > 1) {
+#pragma unroll 1
+        for (; k + UNR <= len; k += UNR) {
+            int c[UNR];
+            T a[UNR];
+            VecR<T, R> xv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) c[u] = ld_op<true>(col + base + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<true>(val + base + 32 * (k + u));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x + (int64_t)c[u] * R);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+#pragma unroll
+                for (int j = 0; j < R; ++j) s.v[j] = fma(a[u], xv[u].v[j], s.v[j]);
+        }
+    }
+#pragma unroll 1
+    for (; k < len; ++k) {
+        const int c = ld_op<true>(col + base + 32 * k);
+        const T a = (T)ld_op<true>(val + base + 32 * k);
+        const VecR<T, R> xv = load_r<T, R>(x + (int64_t)c * R);
+#pragma unroll
+        for (int j = 0; j < R; ++j) s.v[j] = fma(a, xv.v[j], s.v[j]);
+    }
+    return s;
+}
+
+// ---- composite grids ------------------------------------------------------
+
+template <class CI, class T, int R, int UNR, int PF>
+__device__ __forceinline__ VecR<T, R> view_dot_r(const FacViewDev &V, int64_t slice0, int64_t row0, int first,
+                                                 int r, const T *__restrict__ x)
+{
+    const int v = r - first;
+    return sell_dot_r<CI, T, R, UNR, PF>(V.soff, V.rlen, static_cast<const CI *>(V.col), static_cast<const T *>(V.val),
+                                     slice0 + (v >> 5), v & 31, row0 + r, x);
+}
+
+template <class CI, class T, int R, int UNR, int PF>
+__device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B, const FacLevelDesc &d,
+                                             const FacViewDev &V, int64_t s0, int first, int r0, int r1)
+{
+    T *__restrict__ u = static_cast<T *>(P.u) + d.row0 * R;
+    T *__restrict__ t = static_cast<T *>(P.t) + d.row0 * R;
+    T *__restrict__ dd = static_cast<T *>(P.d) + d.row0 * R;
+    const T *__restrict__ f = static_cast<const T *>(P.f) + d.row0 * R;
+    const T *__restrict__ l1 = static_cast<const T *>(P.l1inv) + d.row0;
+    for_rows(B, first, r0, r1, [&](int r) {
+        const VecR<T, R> s = view_dot_r<CI, T, R, UNR, PF>(V, s0, d.row0, first, r, u);
+#pragma unroll
+        for (int j = 0; j < R; ++j) dd[r * R + j] = (f[r * R + j] - s.v[j]) * l1[r];
+    });
+    __syncthreads();
+    for_rows(B, first, r0, r1, [&](int r) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const T v = dd[r * R + j];
+            u[r * R + j] = u[r * R + j] + v;
+            t[r * R + j] = t[r * R + j] + v;
+        }
+    });
+    __syncthreads();
+}
+
+template <class CI, class T, int R, int UNR, int MINB, int PF>
+__global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
+{
+    Block B;
+    B.tid = threadIdx.x;
+    B.nt = blockDim.x;
+    B.lane = threadIdx.x & 31;
+    B.warp = threadIdx.x >> 5;
+    B.nw = blockDim.x >> 5;
+    T *__restrict__ Pu = static_cast<T *>(P.u);
+    T *__restrict__ Pf = static_cast<T *>(P.f);
+    T *__restrict__ Pt = static_cast<T *>(P.t);
+    T *__restrict__ Ps = static_cast<T *>(P.s);
+    T *__restrict__ Pw = static_cast<T *>(P.w);
+    const T *__restrict__ Pl1 = static_cast<const T *>(P.l1inv);
+    __shared__ int claimed;
+    for (;;) {
+        __syncthreads();
+        if (B.tid == 0) {
+            unsigned sm;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+            int g = -1;
+            for (int probe = 0; probe < P.nbins && g < 0; ++probe) {
+                const int b = (int)((sm + (unsigned)probe) % (unsigned)P.nbins);
+                const int k = atomicAdd(P.ctr + b, 1);
+                if (k < P.bin_off[b + 1] - P.bin_off[b]) g = P.bin_grid[P.bin_off[b] + k];
+            }
+            claimed = g;
+        }
+        __syncthreads();
+        const int p = claimed;
+        if (p < 0) break;
+        const FacLevelDesc *D = P.desc + (int64_t)p * P.nlev;
+        const int L = P.nlev - 1;
+
+        for (int l = 0; l <= L; ++l) {
+            const FacLevelDesc d = D[l];
+            const double *__restrict__ rl = P.r_all + P.level_off[l] * R;
+            for (int r = B.tid; r < d.nBar; r += B.nt) {
+                const int64_t i = d.row0 + r;
+                const int64_t g = P.gmap[i];
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    Pu[i * R + j] = T(0);
+                    Pt[i * R + j] = T(0);
+                    Ps[i * R + j] = T(0);
+                    if (r < d.nReal) Pf[i * R + j] = (T)rl[g * R + j];
+                }
+            }
+        }
+        __syncthreads();
+
+        for (int c = 1; c <= P.nfac; ++c) {
+            for (int l = 0; l < L; ++l) {
+                const FacLevelDesc d = D[l];
+                const FacLevelDesc dn = D[l + 1];
+                if (l > 0) {
+                    T *__restrict__ u = Pu + d.row0 * R;
+                    T *__restrict__ t = Pt + d.row0 * R;
+                    const T *__restrict__ f = Pf + d.row0 * R;
+                    const T *__restrict__ l1 = Pl1 + d.row0;
+                    for (int r = B.tid; r < d.nBar; r += B.nt) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            if (r < d.nC) {
+                                const T v = f[r * R + j] * l1[r];
+                                u[r * R + j] = T(0) + v;
+                                t[r * R + j] = t[r * R + j] + v;
+                            } else {
+                                u[r * R + j] = T(0);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal);
+                } else {
+                    relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, 0, d.nC);
+                    relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
+                }
+                {
+                    const T *__restrict__ t = Pt + d.row0 * R;
+                    const T *__restrict__ s = Ps + d.row0 * R;
+                    T *__restrict__ w = Pw + d.row0 * R;
+                    for_rows(B, 0, 0, d.nBar, [&](int r) {
+                        const VecR<T, R> at = view_dot_r<CI, T, R, UNR, PF>(P.At, d.sAt, d.row0, 0, r, t);
+#pragma unroll
+                        for (int j = 0; j < R; ++j) w[r * R + j] = s[r * R + j] + at.v[j];
+                    });
+                }
+                __syncthreads();
+                {
+                    const T *__restrict__ w = Pw + d.row0 * R;
+                    T *__restrict__ s1 = Ps + dn.row0 * R;
+                    T *__restrict__ f1 = Pf + dn.row0 * R;
+                    const T *__restrict__ u1 = Pu + dn.row0 * R;
+                    for_rows(B, 0, 0, dn.nBar, [&](int r) {
+                        const VecR<T, R> sv = view_dot_r<CI, T, R, UNR, PF>(P.R, dn.sR, dn.row0, 0, r, w);
+#pragma unroll
+                        for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
+                        if (r < dn.nReal) {
+                            if (c > 1) {
+                                const VecR<T, R> au = view_dot_r<CI, T, R, UNR, PF>(P.A, dn.sA, dn.row0, 0, r, u1);
+#pragma unroll
+                                for (int j = 0; j < R; ++j) f1[r * R + j] = (f1[r * R + j] - au.v[j]) - sv.v[j];
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
+                            }
+                        }
+                    });
+                    T *__restrict__ t = Pt + d.row0 * R;
+                    T *__restrict__ s = Ps + d.row0 * R;
+                    for (int r = B.tid; r < d.nBar * R; r += B.nt) {
+                        t[r] = T(0);
+                        s[r] = T(0);
+                    }
+                }
+                __syncthreads();
+            }
+            {
+                const FacLevelDesc d = D[L];
+                const T *__restrict__ f = Pf + d.row0 * R;
+                T *__restrict__ u = Pu + d.row0 * R;
+                for (int e = B.tid; e < P.nL * R; e += B.nt) {
+                    const int I = e / R, j = e % R;
+                    double s = 0.0;
+                    const double *__restrict__ a = P.ainv + (int64_t)I * P.nL;
+                    for (int J = 0; J < P.nL; ++J) s = fma(__ldg(a + J), (double)f[J * R + j], s);
+                    u[I * R + j] = (T)s;
+                }
+            }
+            __syncthreads();
+            for (int l = L - 1; l >= 0; --l) {
+                const FacLevelDesc d = D[l];
+                const FacLevelDesc dn = D[l + 1];
+                T *__restrict__ u = Pu + d.row0 * R;
+                const T *__restrict__ u1 = Pu + dn.row0 * R;
+                for_rows(B, 0, 0, d.nBar, [&](int r) {
+                    const VecR<T, R> pu = view_dot_r<CI, T, R, UNR, PF>(P.P, d.sP, d.row0, 0, r, u1);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) u[r * R + j] = u[r * R + j] + pu.v[j];
+                });
+                __syncthreads();
+                relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
+                relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, 0, d.nC);
+            }
+        }
+
+        const FacLevelDesc d0 = D[0];
+        const int64_t o0 = P.owned0[p], o1 = P.owned0[p + 1];
+        for (int64_t k = o0 + B.tid; k < o1; k += B.nt) {
+            const int64_t i = d0.row0 + P.owned[k];
+            const int64_t g = P.gmap[i];
+#pragma unroll
+            for (int j = 0; j < R; ++j) P.x[g * R + j] = P.x[g * R + j] + (double)Pu[i * R + j];
+        }
+    }
+}
+
+}  // namespace dev
+
+// Variant v of the composite-grid kernel for R columns: entries in flight per
+// row (UNR), resident blocks per SM (MINB) of 512 threads, and the L2
+// prefetch distance in steps (PF, 0 = none).
+//   1: UNR 1, 2 blocks    2: UNR 2, 2 blocks    3: UNR 2, 3 blocks
+//   4: UNR 4, 2 blocks    5: UNR 1, 4 blocks    6: UNR 2, 4 blocks
+//   7: UNR 2, 4 blocks, PF 2    8: UNR 2, 3 blocks, PF 2
+//   9: UNR 2, 4 blocks, PF 4
+// 32-bit local columns (composite levels above 65,535 points) use variant 1.
+constexpr int kMultiVariants = 9;
+
+template <class CI, class T, int R, int UNR, int MINB, int PF = 0>
+cudaError_t launch_fac_r_variant(const FacParams &P, int nsub, cudaStream_t st)
+{
+    auto kern = dev::k_fac_all_grids_r<CI, T, R, UNR, MINB, PF>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0);
+    if (e != cudaSuccess) return e;
+    int ctas = (per_sm < 1 ? 1 : per_sm) * P.nbins;
+    if (ctas > nsub) ctas = nsub;
+    if ((e = cudaMemsetAsync(P.ctr, 0, sizeof(int32_t) * (size_t)P.nbins, st)) != cudaSuccess) return e;
+    kern<<<ctas, 512, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <class T, int R>
+cudaError_t launch_fac_r_typed(const FacParams &P, int nsub, int variant, cudaStream_t st)
+{
+    if (!P.col16) return launch_fac_r_variant<int32_t, T, R, 1, 2>(P, nsub, st);
+    switch (variant) {
+    case 2: return launch_fac_r_variant<uint16_t, T, R, 2, 2>(P, nsub, st);
+    case 3: return launch_fac_r_variant<uint16_t, T, R, 2, 3>(P, nsub, st);
+    case 4: return launch_fac_r_variant<uint16_t, T, R, 4, 2>(P, nsub, st);
+    case 5: return launch_fac_r_variant<uint16_t, T, R, 1, 4>(P, nsub, st);
+    case 6: return launch_fac_r_variant<uint16_t, T, R, 2, 4>(P, nsub, st);
+    case 7: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 2>(P, nsub, st);
+    case 8: return launch_fac_r_variant<uint16_t, T, R, 2, 3, 2>(P, nsub, st);
+    case 9: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 4>(P, nsub, st);
+    default: return launch_fac_r_variant<uint16_t, T, R, 1, 2>(P, nsub, st);
+    }
+}
+
+}  // namespace amgdd

@@ -82,7 +82,12 @@ cudaError_t launch_relax_apply(const int32_t *rowid, int64_t r0, int64_t r1, con
 cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, double *u, cudaStream_t st);
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st);
 // several right-hand sides (nrhs = 2 or 4), vectors stored row by row
-cudaError_t launch_fac_multi(const FacParams &P, int nsub, int nrhs, cudaStream_t st);
+// Composite-grid kernel for nrhs = 1, 2 or 4 columns, variant 1..6 (see
+// fac_multi.cuh); the per-column launchers live in fac_multi_r*.cu.
+cudaError_t launch_fac_multi(const FacParams &P, int nsub, int nrhs, int variant, cudaStream_t st);
+cudaError_t launch_fac_multi_1(const FacParams &P, int nsub, int variant, cudaStream_t st);
+cudaError_t launch_fac_multi_2(const FacParams &P, int nsub, int variant, cudaStream_t st);
+cudaError_t launch_fac_multi_4(const FacParams &P, int nsub, int variant, cudaStream_t st);
 cudaError_t launch_residual_multi(const SellView &A, const double *b, const double *x, double *r, double *partial,
                                   int nblocks, double *out, int nrhs, cudaStream_t st);
 cudaError_t launch_sumsq_multi(const double *v, int64_t n, double *partial, int nblocks, double *out, int nrhs,

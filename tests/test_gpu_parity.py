@@ -311,3 +311,52 @@ def test_hybrid_amgdd_bit_exact(case):
         assert np.array_equal(_host(x), xo), lt
         assert np.allclose(info["history"], ho, rtol=1e-12, atol=0), lt
         s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["poisson3d_24", "kappa3d", "batch3"])
+def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
+    """Every FAC kernel the autotuner may choose (the single-column schedules
+    and the several-column kernel's variants, for 1, 2 and 4 columns) gives
+    the oracle's iterate bit for bit; the autotuner keeps one of them and the
+    solve after it is unchanged."""
+    rp, ci, v, part, nsub, pad, _ = _case(case)
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, precision=precision)
+    n = s.n
+    step = o.amgdd_iteration32 if precision else (lambda b, x, nf: o.amgdd_iteration(b, x, nf))
+    Bh = np.stack([I.uniform_rhs(n, 30 + j) for j in range(4)], axis=1)
+    ref = [step(Bh[:, j], np.zeros(n), 2) for j in range(4)]
+    b = _dev(Bh[:, 0])
+    single = [0, 7] if precision else list(range(9))
+    for k in single + list(range(9, 18)):
+        capi.amgdd_set_fac_kernel(s.h, 1, k)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        capi.amgdd_iterate(s.h, b, x)
+        assert np.array_equal(_host(x), ref[0]), k
+    for nrhs in (2, 4):
+        B = torch.from_numpy(np.ascontiguousarray(Bh[:, :nrhs])).cuda()
+        for k in range(9, 18):
+            capi.amgdd_set_fac_kernel(s.h, nrhs, k)
+            X = torch.zeros((n, nrhs), dtype=torch.float64, device="cuda")
+            capi.amgdd_iterate_multi(s.h, B, X)
+            Xh = _host(X)
+            for j in range(nrhs):
+                assert np.array_equal(Xh[:, j], ref[j]), (nrhs, k, j)
+    for k in ([1, 2, 3, 4, 5, 6, 8] if precision else []) + [18, -1]:
+        with pytest.raises(capi.AmgddError):
+            capi.amgdd_set_fac_kernel(s.h, 1, k)
+    with pytest.raises(capi.AmgddError):
+        capi.amgdd_set_fac_kernel(s.h, 2, 3)      # single-column schedules take one column
+    for nrhs in (1, 4):
+        best, ms = capi.amgdd_autotune(s.h, nrhs, reps=2)
+        applies = ms >= 0
+        assert applies[best] and ms[best] == ms[applies].min()
+        assert applies[9:].all() and (applies[:9].any() == (nrhs == 1))
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = s.solve(b, x, tol=1e-8, max_iter=100)
+    xo = np.zeros(n)
+    for _ in range(info["iterations"]):
+        xo = step(Bh[:, 0], xo, 2)
+    assert np.array_equal(_host(x), xo)
+    s.close()

@@ -234,9 +234,12 @@ WORKLOADS = {
 }
 
 
-def workload(name: str, seed: int = 0, shape=None, box=None):
-    """Matrix, partition and right-hand side of a named synthetic workload."""
+def workload(name: str, seed: int = 0, shape=None, box=None, nsys=None):
+    """Matrix, partition and right-hand side of a named synthetic workload
+    (shape, box, nsys: smaller variants of it for profiling and tests)."""
     w = dict(WORKLOADS[name])
+    if nsys is not None:
+        w["nsys"] = int(nsys)
     if shape is not None:
         w["shape"] = tuple(shape)
     if box is not None:

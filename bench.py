@@ -50,22 +50,35 @@ def _config(w):
     }
 
 
-def _measured_traffic(n_edge):
+# FAC kernel of each autotuner candidate: the single-column kernel (schedules
+# 1-9, source kernels.cu) or the several-column kernel (source fac_multi.cuh)
+FAC_KERNELS = {"k_fac_all_grids": "kernels.cu", "k_fac_all_grids_r": "fac_multi.cuh"}
+
+
+def _fac_kernel(candidate):
+    return "k_fac_all_grids" if candidate is None or candidate < 9 else "k_fac_all_grids_r"
+
+
+def _measured_traffic(n_edge, kernel, candidate):
     """DRAM bytes per FAC launch from the committed ncu summary of the 128^3
-    workload, when the kernel source is unchanged since that capture (sha1 of
-    kernels.cu); None otherwise."""
+    workload for this kernel, when that summary was taken with the same
+    candidate and the kernel source is unchanged since (sha1); None
+    otherwise."""
     if n_edge != 128:
         return None
     import hashlib
-    summ = os.path.join(ROOT, "profiles", "k_fac_all_grids_poisson3d_128_dram.md")
-    src = os.path.join(ROOT, "paper_1906_10575_gb300", "csrc", "kernels.cu")
+    summ = os.path.join(ROOT, "profiles", "%s_poisson3d_128_dram.md" % kernel)
+    src = os.path.join(ROOT, "paper_1906_10575_gb300", "csrc", FAC_KERNELS[kernel])
     try:
         txt = open(summ).read()
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    fields = dict(l.split(": ", 1) for l in txt.splitlines() if l.startswith(("kernels_cu_sha1:", "traffic_bytes")))
-    if fields.get("kernels_cu_sha1") != sha:
+    fields = dict(l.split(": ", 1) for l in txt.splitlines()
+                  if l.startswith(("source_sha1:", "traffic_bytes", "candidate:")))
+    if fields.get("source_sha1") != sha:
+        return None
+    if candidate is not None and fields.get("candidate") not in (None, str(candidate)):
         return None
     return int(fields["traffic_bytes_per_launch"])
 
@@ -280,13 +293,14 @@ def run_extra(args, name, stream, dist, local):
     import torch
     from paper_1906_10575_gb300 import Solver, capi
 
-    w = I.workload(name, seed=0)
+    w = I.workload(name, seed=0, nsys=args.nsys if "nsys" in I.WORKLOADS[name] else None)
     n = int(len(w["rowptr"]) - 1)
     hbm, peak_kind = _peaks()
     multi = "nsys" in I.WORKLOADS[name]
     t0 = time.perf_counter()
     s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
-               precision=1, schedule=args.schedule, stream=stream, max_coarse=16 * (64 if multi else 1))
+               precision=1, schedule=args.schedule, stream=stream,
+               max_coarse=16 * (len(w["edges"]) if multi else 1))
     setup_s = time.perf_counter() - t0
     st = s.stats
     nrhs = w["nrhs"] if multi else 1
@@ -296,9 +310,15 @@ def run_extra(args, name, stream, dist, local):
     solve = (lambda: s.solve_multi(B, X, tol=TOL, max_iter=200, stream=stream)) if multi else \
         (lambda: s.solve(B[:, 0], X[:, 0], tol=TOL, max_iter=200, stream=stream))
     tune = None
-    if not args.no_autotune:
-        best, tms = capi.amgdd_autotune(s.h, nrhs, reps=2, stream=stream)
-        tune = {"best_candidate": best, "ms_per_candidate": [round(float(t), 3) for t in tms]}
+    if args.candidate >= 0:
+        capi.amgdd_set_fac_kernel(s.h, nrhs, args.candidate)
+        tune = {"best_candidate": args.candidate, "ms_per_candidate": None}
+    elif not args.no_autotune:
+        # FP32 composite grids are compared with the oracle within rounding
+        # anyway, so the group-per-row candidates take part here
+        best, tms = capi.amgdd_autotune(s.h, nrhs, reps=2, stream=stream, allow_reordered=True)
+        tune = {"best_candidate": best, "ms_per_candidate": [round(float(t), 3) for t in tms],
+                "reordered_allowed": True}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             X.zero_()
@@ -418,9 +438,13 @@ def main():
                     help="poisson3d_128 (default, the headline) or one of the two larger "
                          "mixed-precision configurations, printed as a line of their own")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="larger workloads: keep the default FAC kernel instead of timing every candidate")
-    ap.add_argument("--autotune", action="store_true",
-                    help="headline workload: time every FAC kernel candidate and keep the fastest")
+                    help="keep the default FAC kernel instead of timing every candidate and "
+                         "keeping the fastest")
+    ap.add_argument("--candidate", type=int, default=-1,
+                    help="use this FAC kernel candidate instead of autotuning (profiling captures)")
+    ap.add_argument("--nsys", type=int, default=64,
+                    help="batched_64: number of systems (default 64, the workload; fewer are for "
+                         "profiling captures only)")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="kappa3d_256: skip the FP64 AMG-DD solve used for the final error")
     args = ap.parse_args()
@@ -459,9 +483,13 @@ def main():
     b = torch.from_numpy(w["b"]).cuda()
     x = torch.zeros_like(b)
     tune = None
-    if args.autotune:
-        best, tms = capi.amgdd_autotune(s.h, 1, reps=2, stream=stream)
-        tune = {"best_candidate": best, "ms_per_candidate": [round(float(t), 3) for t in tms]}
+    cand = None
+    if args.candidate >= 0:
+        cand = args.candidate
+        capi.amgdd_set_fac_kernel(s.h, 1, cand)
+    elif not args.no_autotune:
+        cand, tms = capi.amgdd_autotune(s.h, 1, reps=2, stream=stream)
+        tune = {"best_candidate": cand, "ms_per_candidate": [round(float(t), 3) for t in tms]}
 
     def barrier():
         if dist is not None:
@@ -535,6 +563,9 @@ def main():
         s.close()
         sm = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
                     precision=1, stream=stream)
+        cand_m = None
+        if not args.no_autotune:
+            cand_m, _ = capi.amgdd_autotune(sm.h, 1, reps=2, stream=stream)
         with torch.cuda.stream(stream):
             def tm(k):
                 ts, inf = [], None
@@ -569,6 +600,7 @@ def main():
                  "fac_ms_per_launch": round(fac_m, 3),
                  "fac_gbs_algorithmic_fp32": round(algorithmic_fac_bytes(sm.stats, w["n_fac"], sv=4.0)
                                                    / (fac_m * 1e-3) / 1e9, 1),
+                 "fac_candidate": cand_m,
                  "dtype": "f32 AlgFAC / f64 refinement"}
         sm.close()
 
@@ -594,6 +626,9 @@ def main():
                     stream=stream)
         Bm = torch.from_numpy(np.ascontiguousarray(np.stack([I.uniform_rhs(sq.n, j) for j in range(4)], 1))).cuda()
         Xm = torch.zeros_like(Bm)
+        cand_q = None
+        if not args.no_autotune:
+            cand_q, _ = capi.amgdd_autotune(sq.h, 4, reps=2, stream=stream)
         with torch.cuda.stream(stream):
             def tmm(k):
                 ts, inf = [], None
@@ -622,7 +657,7 @@ def main():
         ms_mm = max_over_ranks([statistics.median(t_mm)], dist)[0]
         multi = {"nrhs": 4, "ms_all_columns": round(ms_mm, 3), "ms_per_column": round(ms_mm / 4, 3),
                  "iterations": i_mm["iterations"], "final_relres_max": i_mm["final_relres"],
-                 "ms_per_iteration": round(it_mm, 3),
+                 "ms_per_iteration": round(it_mm, 3), "fac_candidate": cand_q,
                  "dtype": "f64"}
         sq.close()
 
@@ -647,7 +682,8 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": round(fac_gbs, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(frac_hbm, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
-    roof.update({"kernel": "k_fac_all_grids", "traffic": _measured_traffic(args.n),
+    kern = _fac_kernel(cand)
+    roof.update({"kernel": kern, "candidate": cand, "traffic": _measured_traffic(args.n, kern, cand),
                  "ms_per_launch": round(fac_ms, 3),
                  "algorithmic_bytes": fac_b, "algorithmic_flops": fac_f,
                  "hbm_frac_of_measured": round(frac_hbm, 4), "fp64_frac_of_nominal": round(frac_alu, 4),

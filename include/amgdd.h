@@ -277,8 +277,20 @@ amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32
  *               9: 1/2, 10: 2/2, 11: 2/3, 12: 4/2, 13: 1/4, 14: 2/4; and with
  *               the operator entries 2 or 4 steps ahead prefetched into L2:
  *               15: 2/4 (2 ahead), 16: 2/3 (2 ahead), 17: 2/4 (4 ahead).
+ *   k = 18, 19: candidate 16 with g lanes per row ("warp-per-row" for
+ *               g = 32) instead of one: lane j of a group sums entries j,
+ *               j+g, ... and the group adds its partial sums by an xor
+ *               butterfly, so a small level's rows spread over all warps.
+ *               18: g per level from the level's size (g doubles, up to 32,
+ *               while mean slices of 32 rows per grid times g stay below 16
+ *               and 2g stays within the mean row length; 1 on large levels);
+ *               19: g = 32 on every level. These two REORDER each row sum:
+ *               results then differ from the other candidates by rounding
+ *               (they need 16-bit local columns).
  * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
-#define AMGDD_FAC_CANDIDATES 18
+#define AMGDD_FAC_CANDIDATES 20
+/* amgdd_autotune flags: also time candidates 18 and 19 */
+#define AMGDD_TUNE_ALLOW_REORDERED 1
 
 /* Uses candidate k for the FAC step of nrhs (1, 2 or 4) columns from now on.
  * Returns AMGDD_ERR_INVALID_ARG when k does not apply (see above). Drops the
@@ -289,11 +301,14 @@ amgdd_status amgdd_set_fac_kernel(amgdd_handle h, int32_t nrhs, int32_t candidat
  * that applies to nrhs (1, 2 or 4) columns on this handle's composite grids
  * (zero restricted residuals, a scratch solution allocated and freed here),
  * with CUDA events on `stream`, and keeps the fastest as amgdd_set_fac_kernel
- * would. ms (HOST, may be NULL): AMGDD_FAC_CANDIDATES doubles, the mean
- * milliseconds per launch, -1 where a candidate does not apply. best (may be
- * NULL): the chosen candidate. Overwrites the FAC work space (what
- * amgdd_get_fac_state reads) and the handle's residual buffers. */
-amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, double *ms, int32_t *best, void *stream);
+ * would. Candidates that reorder row sums take part only with flags &
+ * AMGDD_TUNE_ALLOW_REORDERED. ms (HOST, may be NULL): AMGDD_FAC_CANDIDATES
+ * doubles, the mean milliseconds per launch, -1 where a candidate does not
+ * apply or was not timed. best (may be NULL): the chosen candidate.
+ * Overwrites the FAC work space (what amgdd_get_fac_state reads) and the
+ * handle's residual buffers. */
+amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, int32_t flags, double *ms, int32_t *best,
+                            void *stream);
 
 /* ---- adjoint: gradient with respect to diffusion coefficients -------------
  * The paper has no adjoint; this supports differentiating solves of the 3D

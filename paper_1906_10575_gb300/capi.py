@@ -66,7 +66,8 @@ EXPORTS = [
     "amgdd_set_fac_kernel", "amgdd_autotune",
 ]
 
-FAC_CANDIDATES = 18
+FAC_CANDIDATES = 20
+TUNE_ALLOW_REORDERED = 1
 
 _lib = None
 
@@ -103,7 +104,7 @@ def load(path: str = LIB_PATH):
         "amgdd_iterate_multi": [vp, vp, vp, i32, vp],
         "amgdd_fac_multi": [vp, vp, vp, i32, vp],
         "amgdd_set_fac_kernel": [vp, i32, i32],
-        "amgdd_autotune": [vp, i32, i32, vp, C.POINTER(i32), vp],
+        "amgdd_autotune": [vp, i32, i32, i32, vp, C.POINTER(i32), vp],
         "amg_hybrid_cycle": [vp, vp, vp, vp],
         "amgdd_kappa_grad_3d": [i32, i32, i32, vp, vp, vp, vp, vp],
         "amg_hybrid_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
@@ -306,12 +307,15 @@ def amgdd_set_fac_kernel(h, nrhs, candidate):
     _check(load().amgdd_set_fac_kernel(h, int(nrhs), int(candidate)), h)
 
 
-def amgdd_autotune(h, nrhs=1, reps=3, stream=None):
-    """Times every FAC kernel candidate for nrhs columns and keeps the fastest.
-    Returns (best candidate, array of ms per candidate, -1 where n/a)."""
+def amgdd_autotune(h, nrhs=1, reps=3, stream=None, allow_reordered=False):
+    """Times every FAC kernel candidate for nrhs columns and keeps the fastest
+    (with allow_reordered, also the group-per-row candidates whose row sums
+    round differently). Returns (best candidate, ms per candidate, -1 where
+    not timed)."""
     ms = np.zeros(FAC_CANDIDATES, np.float64)
     best = C.c_int32(-1)
-    _check(load().amgdd_autotune(h, int(nrhs), int(reps), ms.ctypes.data, C.byref(best), _stream(stream)), h)
+    flags = TUNE_ALLOW_REORDERED if allow_reordered else 0
+    _check(load().amgdd_autotune(h, int(nrhs), int(reps), flags, ms.ctypes.data, C.byref(best), _stream(stream)), h)
     return int(best.value), ms
 
 

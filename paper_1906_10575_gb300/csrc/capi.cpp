@@ -48,6 +48,8 @@ struct amgdd_handle_s {
     int64_t dev_bytes = 0;
     std::vector<DevLevel> lev;
     const double *ainv = nullptr;
+    const int32_t *ainv_ptr = nullptr, *ainv_col = nullptr;   // its nonzeros, by row
+    const double *ainv_val = nullptr;
     int nL = 0;
     FacParams fac{};
     double *r_all = nullptr;            // sum_l n_l
@@ -79,11 +81,11 @@ struct amgdd_handle_s {
     FacParams fac_base{};
     // hybrid AMG-DD (Algorithm 3): composite grids of the hierarchy from level
     // hyb_level down, the residual of that level and its restrictions
-    // FAC kernel per column count (index 0: 1 column, 1: 2, 2: 4): for one
-    // column 0 selects the single-column kernel (schedule in fac.schedule),
-    // v >= 1 the several-column kernel's variant v; for 2 and 4 columns the
-    // several-column kernel's variant
-    int fac_variant[3] = {0, 1, 1};
+    // FAC kernel candidate per column count (index 0: 1 column, 1: 2, 2: 4),
+    // numbered as in amgdd_autotune; and the lanes per row of each level that
+    // the group-per-row candidate uses (chosen from the level sizes at setup)
+    int fac_cand[3] = {7, 9, 9};
+    int8_t grp_level[kMaxLevels + 1] = {};
     int hyb_level = -1;
     FacParams fac_hyb{};
     double *r_hyb = nullptr;
@@ -387,6 +389,26 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, FacStream &S, int nl
     UP(F.owned0, &o0, "upload owned0");
     P.col16 = F.A.c16 ? 1 : 0;
     P.schedule = h->opt.schedule >= 1 && h->opt.schedule <= 9 ? h->opt.schedule : 8;
+    for (int l = 0; l <= kMaxLevels; ++l) P.grp[l] = 1;
+    // lanes per row for the group-per-row candidate, per level: double g
+    // (up to 32) while the level's mean slices per grid times g stay below
+    // the 16 warps of a block and 2g entries still fit the mean real row
+    if (&P == &h->fac) {
+        h->fac_cand[0] = P.schedule - 1;   // the options' schedule until changed
+        for (int l = 0; l < nlev && l <= kMaxLevels; ++l) {
+            double slices = 0.0, rows = 0.0;
+            for (int p = 0; p < nsub; ++p) {
+                const FacLevelDesc &d = F.desc[(size_t)p * nlev + l];
+                slices += (double)((d.nBar + 31) / 32);
+                rows += (double)d.nReal;
+            }
+            slices /= std::max(nsub, 1);
+            const double width = rows > 0 ? (double)F.lvA[l] / rows : 0.0;
+            int g = 1;
+            while (g < 32 && slices * g < 16.0 && 2.0 * g <= width) g *= 2;
+            h->grp_level[l] = (int8_t)g;
+        }
+    }
     FacViewDev *dviews[5] = {&P.A, &P.At, &P.AFc, &P.P, &P.R};
     void *gm = nullptr, *l1 = nullptr;
     *what = "settle layout";
@@ -443,6 +465,9 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, FacStream &S, int nl
     P.owned = own;
     P.owned0 = o0;
     P.ainv = h->ainv;
+    P.ainv_ptr = h->ainv_ptr;
+    P.ainv_col = h->ainv_col;
+    P.ainv_val = h->ainv_val;
     for (int l = 0; l <= kMaxLevels; ++l) P.level_off[l] = l <= nlev ? level_off[l] : 0;
     void *ws[6];
     for (int k = 0; k < 6; ++k) {
@@ -719,6 +744,30 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             double *ainv;
             if ((e = upload(h, h->H.ainv, &ainv, st_)) != cudaSuccess) return bail(e, "upload coarse inverse");
             h->ainv = ainv;
+            {
+                const int64_t nL = h->H.lv.back().A.rows;
+                std::vector<int32_t> cp(1, 0), cc;
+                std::vector<double> cv;
+                for (int64_t I = 0; I < nL; ++I) {
+                    for (int64_t J = 0; J < nL; ++J) {
+                        const double a = h->H.ainv[(size_t)(I * nL + J)];
+                        if (a != 0.0) {
+                            cc.push_back((int32_t)J);
+                            cv.push_back(a);
+                        }
+                    }
+                    cp.push_back((int32_t)cc.size());
+                }
+                int32_t *dp, *dc;
+                double *dv;
+                if ((e = upload(h, cp, &dp, st_)) != cudaSuccess) return bail(e, "upload coarse inverse");
+                if ((e = upload(h, cc, &dc, st_)) != cudaSuccess) return bail(e, "upload coarse inverse");
+                if ((e = upload(h, cv, &dv, st_)) != cudaSuccess) return bail(e, "upload coarse inverse");
+                if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return bail(e, "upload coarse inverse");
+                h->ainv_ptr = dp;
+                h->ainv_col = dc;
+                h->ainv_val = dv;
+            }
             h->nL = h->H.lv.back().A.rows;
             if ((e = alloc(h, (size_t)h->level_off.back(), &h->r_all)) != cudaSuccess) return bail(e, "alloc r");
             if ((e = alloc(h, maxn, &h->res)) != cudaSuccess) return bail(e, "alloc res");
@@ -860,13 +909,26 @@ static amgdd_status restrict_all(amgdd_handle h, double *r_all, cudaStream_t st)
     return AMGDD_OK;
 }
 
+// FAC launch of candidate k (see amgdd_autotune) for nrhs columns with the
+// inputs, outputs and work space already set in P.
+static cudaError_t launch_candidate(amgdd_handle h, FacParams P, int nrhs, int k, cudaStream_t st)
+{
+    for (int l = 0; l <= kMaxLevels; ++l) P.grp[l] = 1;
+    if (k < 9) {
+        P.schedule = k + 1;
+        return launch_fac_all_grids(P, P.nsub, h->threads, st);
+    }
+    if (k < 18) return launch_fac_multi(P, P.nsub, nrhs, k - 8, st);
+    for (int l = 0; l <= kMaxLevels; ++l) P.grp[l] = k == 18 ? h->grp_level[l] : (int8_t)32;
+    return launch_fac_multi(P, P.nsub, nrhs, 10, st);
+}
+
 static amgdd_status fac(amgdd_handle h, const double *r_all, double *x, cudaStream_t st)
 {
     FacParams P = h->fac;
     P.r_all = r_all;
     P.x = x;
-    if (h->fac_variant[0] > 0) CK(launch_fac_multi(P, P.nsub, 1, h->fac_variant[0], st), "FAC kernel");
-    else CK(launch_fac_all_grids(P, P.nsub, h->threads, st), "FAC kernel");
+    CK(launch_candidate(h, P, 1, h->fac_cand[0], st), "FAC kernel");
     h->launches += 1;
     return AMGDD_OK;
 }
@@ -1165,7 +1227,7 @@ static amgdd_status iterate_multi(amgdd_handle h, amgdd_handle_s::Multi &m, cons
     P.u = m.ws[0]; P.f = m.ws[1]; P.t = m.ws[2]; P.s = m.ws[3]; P.w = m.ws[4]; P.d = m.ws[5];
     P.r_all = m.r_all;
     P.x = X;
-    CK(launch_fac_multi(P, P.nsub, R, h->fac_variant[R == 2 ? 1 : 2], st), "FAC kernel");
+    CK(launch_candidate(h, P, R, h->fac_cand[R == 2 ? 1 : 2], st), "FAC kernel");
     h->launches += 1;
     return AMGDD_OK;
 }
@@ -1194,7 +1256,7 @@ amgdd_status amgdd_fac_multi(amgdd_handle h, const double *R_all, double *X, int
     P.u = m->ws[0]; P.f = m->ws[1]; P.t = m->ws[2]; P.s = m->ws[3]; P.w = m->ws[4]; P.d = m->ws[5];
     P.r_all = R_all;
     P.x = X;
-    CK(launch_fac_multi(P, P.nsub, nrhs, h->fac_variant[nrhs == 2 ? 1 : 2], st), "FAC kernel");
+    CK(launch_candidate(h, P, nrhs, h->fac_cand[nrhs == 2 ? 1 : 2], st), "FAC kernel");
     h->launches += 1;
     return AMGDD_OK;
 }
@@ -1329,14 +1391,18 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
 
 // Candidate k of amgdd_autotune / amgdd_set_fac_kernel: k < 9 is the
 // single-column kernel with schedule k + 1 (one column only; FP32 composite
-// grids have schedules 1 and 8), k >= 9 the several-column kernel's variant
-// k - 8.
+// grids have schedules 1 and 8), 9 <= k < 18 the several-column kernel's
+// variant k - 8, 18 and 19 its group-per-row variant (lanes per row by level
+// size, or 32 on every level), whose row sums are not the ascending chain.
 static bool candidate_applies(amgdd_handle h, int nrhs, int k)
 {
     if (k < 0 || k >= AMGDD_FAC_CANDIDATES) return false;
     if (k < 9) return nrhs == 1 && (!h->fac.fp32 || k == 0 || k == 7);
+    if (k >= 18) return h->fac.col16 != 0;
     return true;
 }
+
+static bool candidate_reorders(int k) { return k >= 18; }
 
 static void drop_graphs(amgdd_handle h)
 {
@@ -1354,13 +1420,7 @@ static void drop_graphs(amgdd_handle h)
 
 static void apply_candidate(amgdd_handle h, int nrhs, int k)
 {
-    const int idx = nrhs == 1 ? 0 : nrhs == 2 ? 1 : 2;
-    if (k < 9) {
-        h->fac_variant[0] = 0;
-        h->fac.schedule = k + 1;
-    } else {
-        h->fac_variant[idx] = k - 8;
-    }
+    h->fac_cand[nrhs == 1 ? 0 : nrhs == 2 ? 1 : 2] = k;
 }
 
 amgdd_status amgdd_set_fac_kernel(amgdd_handle h, int32_t nrhs, int32_t candidate)
@@ -1376,7 +1436,8 @@ amgdd_status amgdd_set_fac_kernel(amgdd_handle h, int32_t nrhs, int32_t candidat
     return AMGDD_OK;
 }
 
-amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, double *ms, int32_t *best, void *stream)
+amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, int32_t flags, double *ms, int32_t *best,
+                            void *stream)
 {
     amgdd_status s = require_device(h);
     if (s != AMGDD_OK) return s;
@@ -1406,14 +1467,8 @@ amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, double *
     for (int k = 0; k < AMGDD_FAC_CANDIDATES && e == cudaSuccess; ++k) {
         if (ms) ms[k] = -1.0;
         if (!candidate_applies(h, nrhs, k)) continue;
-        FacParams Q = P;
-        auto launch = [&]() -> cudaError_t {
-            if (k < 9) {
-                Q.schedule = k + 1;
-                return launch_fac_all_grids(Q, Q.nsub, h->threads, st);
-            }
-            return launch_fac_multi(Q, Q.nsub, nrhs, k - 8, st);
-        };
+        if (candidate_reorders(k) && !(flags & AMGDD_TUNE_ALLOW_REORDERED)) continue;
+        auto launch = [&]() -> cudaError_t { return launch_candidate(h, P, nrhs, k, st); };
         if ((e = launch()) != cudaSuccess) break;           // warm-up
         if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();

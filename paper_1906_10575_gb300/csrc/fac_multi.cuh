@@ -132,8 +132,66 @@ __device__ __forceinline__ VecR<T, R> view_dot_r(const FacViewDev &V, int64_t sl
                                      slice0 + (v >> 5), v & 31, row0 + r, x);
 }
 
-template <class CI, class T, int R, int UNR, int PF>
-__device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B, const FacLevelDesc &d,
+// Row products V_r . x of local rows [r0, r1) of a view whose slices start at
+// local row `first`; fn(r, s) is called once per row (by one lane).
+// g == 1 (tile): one row per lane of a SELL-32 slice, the single-column chain.
+// g > 1 (GRP builds only): g lanes per row, lane j of the group sums entries
+// j, j + g, j + 2g, ... of the row, then the group adds its g partial sums by
+// an xor butterfly. The warp covers 32 / g consecutive rows of one slice per
+// pass, so rows of small levels spread over all warps and each lane's chain
+// is g times shorter; the rounding order is not the ascending chain's.
+template <class CI, class T, int R, int UNR, int PF, bool GRP, class Fn>
+__device__ __forceinline__ void rows_dot(const Block &B, int g, const FacViewDev &V, int64_t s0, int64_t row0,
+                                         int first, int r0, int r1, const T *__restrict__ x, Fn &&fn)
+{
+    if (!GRP || g <= 1) {
+        for_rows(B, first, r0, r1, [&](int r) { fn(r, view_dot_r<CI, T, R, UNR, PF>(V, s0, row0, first, r, x)); });
+        return;
+    }
+    if (r1 <= r0) return;
+    const int rpw = 32 / g;
+    const int sub = B.lane / g, j = B.lane & (g - 1);
+    const int u0 = (r0 - first) / rpw, u1 = (r1 - first + rpw - 1) / rpw;
+    const CI *__restrict__ col = static_cast<const CI *>(V.col);
+    const T *__restrict__ val = static_cast<const T *>(V.val);
+    for (int uu = u0 + B.warp; uu < u1; uu += B.nw) {
+        const int r = first + uu * rpw + sub;
+        const bool on = r >= r0 && r < r1;
+        VecR<T, R> acc;
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc.v[q] = T(0);
+        if (on) {
+            const int v = r - first;
+            const int64_t base = __ldg(V.soff + s0 + (v >> 5)) + (v & 31);
+            const int len = __ldg(V.rlen + row0 + r);
+            int k = j;
+#pragma unroll 1
+            for (; k + g < len; k += 2 * g) {
+                const int c0 = ld_op<true>(col + base + 32 * k), c1 = ld_op<true>(col + base + 32 * (k + g));
+                const T a0 = ld_op<true>(val + base + 32 * k), a1 = ld_op<true>(val + base + 32 * (k + g));
+                const VecR<T, R> x0 = load_r<T, R>(x + (int64_t)c0 * R), x1 = load_r<T, R>(x + (int64_t)c1 * R);
+#pragma unroll
+                for (int q = 0; q < R; ++q) acc.v[q] = fma(a0, x0.v[q], acc.v[q]);
+#pragma unroll
+                for (int q = 0; q < R; ++q) acc.v[q] = fma(a1, x1.v[q], acc.v[q]);
+            }
+            if (k < len) {
+                const int c0 = ld_op<true>(col + base + 32 * k);
+                const T a0 = ld_op<true>(val + base + 32 * k);
+                const VecR<T, R> x0 = load_r<T, R>(x + (int64_t)c0 * R);
+#pragma unroll
+                for (int q = 0; q < R; ++q) acc.v[q] = fma(a0, x0.v[q], acc.v[q]);
+            }
+        }
+        for (int m = 1; m < g; m <<= 1)
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc.v[q] = acc.v[q] + __shfl_xor_sync(0xffffffffu, acc.v[q], m);
+        if (on && j == 0) fn(r, acc);
+    }
+}
+
+template <class CI, class T, int R, int UNR, int PF, bool GRP>
+__device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B, const FacLevelDesc &d, int g,
                                              const FacViewDev &V, int64_t s0, int first, int r0, int r1)
 {
     T *__restrict__ u = static_cast<T *>(P.u) + d.row0 * R;
@@ -141,8 +199,7 @@ __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B,
     T *__restrict__ dd = static_cast<T *>(P.d) + d.row0 * R;
     const T *__restrict__ f = static_cast<const T *>(P.f) + d.row0 * R;
     const T *__restrict__ l1 = static_cast<const T *>(P.l1inv) + d.row0;
-    for_rows(B, first, r0, r1, [&](int r) {
-        const VecR<T, R> s = view_dot_r<CI, T, R, UNR, PF>(V, s0, d.row0, first, r, u);
+    rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, u, [&](int r, const VecR<T, R> &s) {
 #pragma unroll
         for (int j = 0; j < R; ++j) dd[r * R + j] = (f[r * R + j] - s.v[j]) * l1[r];
     });
@@ -158,7 +215,7 @@ __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B,
     __syncthreads();
 }
 
-template <class CI, class T, int R, int UNR, int MINB, int PF>
+template <class CI, class T, int R, int UNR, int MINB, int PF, bool GRP>
 __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
 {
     Block B;
@@ -214,6 +271,7 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
             for (int l = 0; l < L; ++l) {
                 const FacLevelDesc d = D[l];
                 const FacLevelDesc dn = D[l + 1];
+                const int gl = GRP ? P.grp[l] : 1, gn = GRP ? P.grp[l + 1] : 1;
                 if (l > 0) {
                     T *__restrict__ u = Pu + d.row0 * R;
                     T *__restrict__ t = Pt + d.row0 * R;
@@ -232,17 +290,17 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                         }
                     }
                     __syncthreads();
-                    relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.AFc, d.sAFc, d.nC, d.nC, d.nReal);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal);
                 } else {
-                    relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, 0, d.nC);
-                    relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal);
                 }
                 {
                     const T *__restrict__ t = Pt + d.row0 * R;
                     const T *__restrict__ s = Ps + d.row0 * R;
                     T *__restrict__ w = Pw + d.row0 * R;
-                    for_rows(B, 0, 0, d.nBar, [&](int r) {
-                        const VecR<T, R> at = view_dot_r<CI, T, R, UNR, PF>(P.At, d.sAt, d.row0, 0, r, t);
+                    rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.At, d.sAt, d.row0, 0, 0, d.nBar, t,
+                                                     [&](int r, const VecR<T, R> &at) {
 #pragma unroll
                         for (int j = 0; j < R; ++j) w[r * R + j] = s[r * R + j] + at.v[j];
                     });
@@ -253,21 +311,47 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                     T *__restrict__ s1 = Ps + dn.row0 * R;
                     T *__restrict__ f1 = Pf + dn.row0 * R;
                     const T *__restrict__ u1 = Pu + dn.row0 * R;
-                    for_rows(B, 0, 0, dn.nBar, [&](int r) {
-                        const VecR<T, R> sv = view_dot_r<CI, T, R, UNR, PF>(P.R, dn.sR, dn.row0, 0, r, w);
+                    // s_{l+1} = R_l w_l on every row of level l+1; then, on its
+                    // real rows, f_{l+1} -= A_{l+1} u_{l+1} (cycles after the
+                    // first) and f_{l+1} -= s_{l+1}
+                    if (!GRP || gn <= 1) {
+                        for_rows(B, 0, 0, dn.nBar, [&](int r) {
+                            const VecR<T, R> sv = view_dot_r<CI, T, R, UNR, PF>(P.R, dn.sR, dn.row0, 0, r, w);
 #pragma unroll
-                        for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
-                        if (r < dn.nReal) {
-                            if (c > 1) {
-                                const VecR<T, R> au = view_dot_r<CI, T, R, UNR, PF>(P.A, dn.sA, dn.row0, 0, r, u1);
+                            for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
+                            if (r < dn.nReal) {
+                                if (c > 1) {
+                                    const VecR<T, R> au =
+                                        view_dot_r<CI, T, R, UNR, PF>(P.A, dn.sA, dn.row0, 0, r, u1);
 #pragma unroll
-                                for (int j = 0; j < R; ++j) f1[r * R + j] = (f1[r * R + j] - au.v[j]) - sv.v[j];
-                            } else {
+                                    for (int j = 0; j < R; ++j)
+                                        f1[r * R + j] = (f1[r * R + j] - au.v[j]) - sv.v[j];
+                                } else {
+#pragma unroll
+                                    for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
+                                }
+                            }
+                        });
+                    } else {
+                        // groups: two traversals; row r has the same owning
+                        // lane in both, which reads back its own s_{l+1}
+                        rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.R, dn.sR, dn.row0, 0, 0, dn.nBar, w,
+                                                         [&](int r, const VecR<T, R> &sv) {
+#pragma unroll
+                            for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
+                            if (c == 1 && r < dn.nReal) {
 #pragma unroll
                                 for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
                             }
-                        }
-                    });
+                        });
+                        if (c > 1)
+                            rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.A, dn.sA, dn.row0, 0, 0, dn.nReal, u1,
+                                                             [&](int r, const VecR<T, R> &au) {
+#pragma unroll
+                                for (int j = 0; j < R; ++j)
+                                    f1[r * R + j] = (f1[r * R + j] - au.v[j]) - s1[r * R + j];
+                            });
+                    }
                     T *__restrict__ t = Pt + d.row0 * R;
                     T *__restrict__ s = Ps + d.row0 * R;
                     for (int r = B.tid; r < d.nBar * R; r += B.nt) {
@@ -281,11 +365,15 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                 const FacLevelDesc d = D[L];
                 const T *__restrict__ f = Pf + d.row0 * R;
                 T *__restrict__ u = Pu + d.row0 * R;
+                // u_L = A_L^{-1} f_L in FP64 over the nonzeros of the inverse:
+                // the chain starts at +0 and never returns to -0, so each
+                // skipped fma(0, f_J, s) would have left s unchanged (finite f)
                 for (int e = B.tid; e < P.nL * R; e += B.nt) {
                     const int I = e / R, j = e % R;
                     double s = 0.0;
-                    const double *__restrict__ a = P.ainv + (int64_t)I * P.nL;
-                    for (int J = 0; J < P.nL; ++J) s = fma(__ldg(a + J), (double)f[J * R + j], s);
+                    const int32_t k1 = __ldg(P.ainv_ptr + I + 1);
+                    for (int32_t k = __ldg(P.ainv_ptr + I); k < k1; ++k)
+                        s = fma(__ldg(P.ainv_val + k), (double)f[__ldg(P.ainv_col + k) * R + j], s);
                     u[I * R + j] = (T)s;
                 }
             }
@@ -295,14 +383,15 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                 const FacLevelDesc dn = D[l + 1];
                 T *__restrict__ u = Pu + d.row0 * R;
                 const T *__restrict__ u1 = Pu + dn.row0 * R;
-                for_rows(B, 0, 0, d.nBar, [&](int r) {
-                    const VecR<T, R> pu = view_dot_r<CI, T, R, UNR, PF>(P.P, d.sP, d.row0, 0, r, u1);
+                const int gl = GRP ? P.grp[l] : 1;
+                rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.P, d.sP, d.row0, 0, 0, d.nBar, u1,
+                                                 [&](int r, const VecR<T, R> &pu) {
 #pragma unroll
                     for (int j = 0; j < R; ++j) u[r * R + j] = u[r * R + j] + pu.v[j];
                 });
                 __syncthreads();
-                relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, d.nC, d.nReal);
-                relax_pass_r<CI, T, R, UNR, PF>(P, B, d, P.A, d.sA, 0, 0, d.nC);
+                relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal);
+                relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC);
             }
         }
 
@@ -326,13 +415,15 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
 //   4: UNR 4, 2 blocks    5: UNR 1, 4 blocks    6: UNR 2, 4 blocks
 //   7: UNR 2, 4 blocks, PF 2    8: UNR 2, 3 blocks, PF 2
 //   9: UNR 2, 4 blocks, PF 4
+//  10: UNR 2, 3 blocks, PF 2, with g lanes per row on level l where
+//      P.grp[l] = g > 1
 // 32-bit local columns (composite levels above 65,535 points) use variant 1.
-constexpr int kMultiVariants = 9;
+constexpr int kMultiVariants = 10;
 
-template <class CI, class T, int R, int UNR, int MINB, int PF = 0>
+template <class CI, class T, int R, int UNR, int MINB, int PF = 0, bool GRP = false>
 cudaError_t launch_fac_r_variant(const FacParams &P, int nsub, cudaStream_t st)
 {
-    auto kern = dev::k_fac_all_grids_r<CI, T, R, UNR, MINB, PF>;
+    auto kern = dev::k_fac_all_grids_r<CI, T, R, UNR, MINB, PF, GRP>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0);
     if (e != cudaSuccess) return e;
@@ -356,6 +447,7 @@ cudaError_t launch_fac_r_typed(const FacParams &P, int nsub, int variant, cudaSt
     case 7: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 2>(P, nsub, st);
     case 8: return launch_fac_r_variant<uint16_t, T, R, 2, 3, 2>(P, nsub, st);
     case 9: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 4>(P, nsub, st);
+    case 10: return launch_fac_r_variant<uint16_t, T, R, 2, 3, 2, true>(P, nsub, st);
     default: return launch_fac_r_variant<uint16_t, T, R, 1, 2>(P, nsub, st);
     }
 }

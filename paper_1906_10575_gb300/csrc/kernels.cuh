@@ -63,11 +63,19 @@ struct FacParams {
     const int32_t *owned;       // level-0 local indices of owned points
     const int64_t *owned0;      // per grid offset (nsub + 1)
     const double *ainv;         // n_L x n_L
+    // the nonzeros of ainv row by row, ascending columns (nL + 1 offsets);
+    // a block-diagonal coarsest level (independent systems) leaves most of
+    // the dense inverse exactly zero
+    const int32_t *ainv_ptr, *ainv_col;
+    const double *ainv_val;
     const double *r_all;        // restricted residuals, levels back to back
     int64_t level_off[kMaxLevels + 1];
     double *x;
     void *u, *f, *t, *s, *w, *d;    // per-row workspace, composite grid's type
     int fp32;                   // 1: composite grids in FP32 (mixed precision)
+    // lanes per row on each level in the group-per-row kernel variant
+    // (powers of two up to 32; 1 = one row per lane)
+    int8_t grp[kMaxLevels + 1];
 };
 
 cudaError_t launch_residual(const SellView &A, const double *b, const double *x, double *r, double *partial,

@@ -113,6 +113,42 @@ def diffusion3d(kappa: np.ndarray):
     return _stencil_csr(shape, (c_minus, c_plus))
 
 
+def rotated_anisotropic2d(nx: int, ny: int, theta: float = 3 * np.pi / 16, eps: float = 1e-3):
+    """-div(K grad u) on the unit square, K = Q diag(1, eps) Q^T with Q the
+    rotation by theta, Dirichlet boundary, nx*ny interior nodes, i fastest.
+
+    9-point finite differences (unscaled by h^2): with k11 = cos^2 + eps sin^2,
+    k22 = sin^2 + eps cos^2, k12 = (1 - eps) cos sin, centre 2 k11 + 2 k22,
+    east/west -k11, north/south -k22, and the mixed derivative as
+    -2 k12 (u_NE - u_NW - u_SE + u_SW) / 4: NE/SW -k12/2, NW/SE +k12/2.
+    """
+    c, s = np.cos(theta), np.sin(theta)
+    k11 = c * c + eps * s * s
+    k22 = s * s + eps * c * c
+    k12 = (1.0 - eps) * c * s
+    n = nx * ny
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    ii = ii.reshape(-1)
+    jj = jj.reshape(-1)
+    rows, cols, vals = [np.arange(n)], [np.arange(n)], [np.full(n, 2.0 * k11 + 2.0 * k22)]
+    for di, dj, a in ((-1, 0, -k11), (1, 0, -k11), (0, -1, -k22), (0, 1, -k22),
+                      (1, 1, -0.5 * k12), (-1, -1, -0.5 * k12), (-1, 1, 0.5 * k12), (1, -1, 0.5 * k12)):
+        i2, j2 = ii + di, jj + dj
+        ok = (i2 >= 0) & (i2 < nx) & (j2 >= 0) & (j2 < ny)
+        rows.append(np.nonzero(ok)[0])
+        cols.append(j2[ok] * nx + i2[ok])
+        vals.append(np.full(int(ok.sum()), a))
+    r = np.concatenate(rows)
+    cidx = np.concatenate(cols)
+    v = np.concatenate(vals)
+    order = np.lexsort((cidx, r))
+    r, cidx, v = r[order], cidx[order], v[order]
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr.astype(np.int32), cidx.astype(np.int32), v
+
+
 def checkerboard_kappa(n: int, blocks: int, seed: int, values=(1.0, 1e3)):
     """Piecewise-constant kappa on an n^3 grid: blocks^3 cubes, i.i.d. values."""
     rng = np.random.default_rng(seed)
@@ -226,6 +262,10 @@ WORKLOADS = {
     # FP32 AlgFAC inside FP64 refinement
     "kappa3d_256": dict(shape=(256, 256, 256), box=(16, 16, 16), padding=2, n_fac=2,
                         kappa_blocks=8, precision=1),
+    # 2D rotated anisotropic diffusion (theta = 3 pi / 16, eps = 1e-3, 9-point
+    # finite differences) on 512^2, 256 boxes of 32^2, padding 2, FP64
+    "aniso2d_512": dict(shape=(512, 512), box=(32, 32), padding=2, n_fac=2,
+                        aniso=(3 * np.pi / 16, 1e-3)),
     # 64 independent 3D 7-point Poisson systems, edges i.i.d. from
     # {32, 48, 64, 80, 96}, boxes of 16^3, 4 right-hand sides each, FP32
     # AlgFAC inside FP64 refinement
@@ -254,6 +294,8 @@ def workload(name: str, seed: int = 0, shape=None, box=None, nsys=None):
     if "kappa_blocks" in w:
         kappa = checkerboard_kappa(shape[0], w["kappa_blocks"], seed)
         rp, ci, v = diffusion3d(kappa)
+    elif "aniso" in w:
+        rp, ci, v = rotated_anisotropic2d(shape[0], shape[1], *w["aniso"])
     elif len(shape) == 2:
         rp, ci, v = poisson2d(*shape)
     else:

@@ -280,7 +280,7 @@ def _ev_ms(stream, fn, k=1):
 
 
 def run_extra(args, name, stream, dist, local):
-    """The two larger configurations, one JSON line each (not the headline):
+    """The other configurations, one JSON line each (not the headline):
 
     kappa3d_256 -- 256^3 variable-coefficient diffusion, 4096 composite grids,
       FP32 AlgFAC inside FP64 refinement; AMG-DD against the FP64 V-cycle on
@@ -289,7 +289,9 @@ def run_extra(args, name, stream, dist, local):
     batched_64 -- 64 independent Poisson systems as one block-diagonal matrix,
       4 right-hand sides, FP32 AlgFAC inside FP64 refinement, one
       several-column FAC launch per iteration in a CUDA graph; against four
-      single-column FP64 V-cycle solves on the same hierarchy."""
+      single-column FP64 V-cycle solves on the same hierarchy.
+    aniso2d_512 -- 2D rotated anisotropic diffusion (the paper's second test
+      problem as finite differences), FP64, AMG-DD against the V-cycle."""
     import torch
     from paper_1906_10575_gb300 import Solver, capi
 
@@ -297,9 +299,11 @@ def run_extra(args, name, stream, dist, local):
     n = int(len(w["rowptr"]) - 1)
     hbm, peak_kind = _peaks()
     multi = "nsys" in I.WORKLOADS[name]
+    prec = int(w.get("precision", 0))
+    maxit = 2000
     t0 = time.perf_counter()
     s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
-               precision=1, schedule=args.schedule, stream=stream,
+               precision=prec, schedule=args.schedule, stream=stream,
                max_coarse=16 * (len(w["edges"]) if multi else 1))
     setup_s = time.perf_counter() - t0
     st = s.stats
@@ -307,18 +311,18 @@ def run_extra(args, name, stream, dist, local):
     Bh = w["B"] if multi else w["b"][:, None]
     B = torch.from_numpy(np.ascontiguousarray(Bh)).cuda()
     X = torch.zeros_like(B)
-    solve = (lambda: s.solve_multi(B, X, tol=TOL, max_iter=200, stream=stream)) if multi else \
-        (lambda: s.solve(B[:, 0], X[:, 0], tol=TOL, max_iter=200, stream=stream))
+    solve = (lambda: s.solve_multi(B, X, tol=TOL, max_iter=maxit, stream=stream)) if multi else \
+        (lambda: s.solve(B[:, 0], X[:, 0], tol=TOL, max_iter=maxit, stream=stream))
     tune = None
     if args.candidate >= 0:
         capi.amgdd_set_fac_kernel(s.h, nrhs, args.candidate)
         tune = {"best_candidate": args.candidate, "ms_per_candidate": None}
     elif not args.no_autotune:
         # FP32 composite grids are compared with the oracle within rounding
-        # anyway, so the group-per-row candidates take part here
-        best, tms = capi.amgdd_autotune(s.h, nrhs, reps=2, stream=stream, allow_reordered=True)
+        # anyway, so there the group-per-row candidates take part
+        best, tms = capi.amgdd_autotune(s.h, nrhs, reps=2, stream=stream, allow_reordered=prec == 1)
         tune = {"best_candidate": best, "ms_per_candidate": [round(float(t), 3) for t in tms],
-                "reordered_allowed": True}
+                "reordered_allowed": prec == 1}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             X.zero_()
@@ -357,16 +361,17 @@ def run_extra(args, name, stream, dist, local):
         for j in range(nrhs):
             bj = B[:, j].contiguous()
             xv.zero_()
-            s.vcycle_solve(bj, xv, tol=TOL, max_iter=200, stream=stream)
+            s.vcycle_solve(bj, xv, tol=TOL, max_iter=maxit, stream=stream)
             xv.zero_()
             torch.cuda.synchronize()
             iv = {}
-            v_ms += _ev_ms(stream, lambda: iv.update(s.vcycle_solve(bj, xv, tol=TOL, max_iter=200, stream=stream)))
+            v_ms += _ev_ms(stream, lambda: iv.update(s.vcycle_solve(bj, xv, tol=TOL, max_iter=maxit,
+                                                                     stream=stream)))
             v_it.append(iv["iterations"])
     s.close()
     ms = statistics.median(times)
     ms, v_ms = max_over_ranks([ms, v_ms], dist)
-    fac_b = algorithmic_fac_bytes(st, w["n_fac"], sv=4.0)
+    fac_b = algorithmic_fac_bytes(st, w["n_fac"], sv=4.0 if prec else 8.0)
     # several columns: the operator once, the vector touches once per column
     if multi:
         L = st.num_levels - 1
@@ -374,13 +379,13 @@ def run_extra(args, name, stream, dist, local):
         fac_b = fac_b + (nrhs - 1) * vec
     fac_gbs = fac_b / (fac_ms * 1e-3) / 1e9
     err = None
-    if not multi and not args.no_fp64_check:
+    if not multi and prec == 1 and not args.no_fp64_check:
         # FP64 AMG-DD on the same problem: reference solution for the error
         s64 = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
                      stream=stream)
         x64 = torch.zeros(n, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
-            i64 = s64.solve(B[:, 0], x64, tol=TOL, max_iter=200, stream=stream)
+            i64 = s64.solve(B[:, 0], x64, tol=TOL, max_iter=maxit, stream=stream)
             torch.cuda.synchronize()
         err = {"rel_error_vs_fp64_amgdd": float(torch.linalg.vector_norm(Xmix[:, 0] - x64)
                                                 / torch.linalg.vector_norm(x64)),
@@ -392,12 +397,16 @@ def run_extra(args, name, stream, dist, local):
                 "boxes of 16^3 (%d subdomains), padding 2, %d right-hand sides U[-1,1], "
                 "FP32 AlgFAC / FP64 refinement" % (len(w["edges"]), ",".join(map(str, sorted(set(w["edges"])))),
                                                      n, w["nsub"], nrhs))
+    elif "aniso" in I.WORKLOADS[name]:
+        desc = ("2D rotated anisotropic diffusion theta=3pi/16, eps=1e-3, 9-point, 512^2 (N=%d), %d subdomains "
+                "of 32^2, padding 2, FP64, b~U[-1,1] seed 0" % (n, w["nsub"]))
     else:
         desc = ("3D 7-point diffusion 256^3 (N=%d), kappa on 8^3 blocks of 32^3 i.i.d. {1,1e3}, %d subdomains "
                 "of 16^3, padding 2, FP32 AlgFAC / FP64 refinement, b~U[-1,1] seed 0" % (n, w["nsub"]))
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "higher_is_better": False, "dtype": "f32 AlgFAC / f64 refinement",
+        "warmup": args.warmup, "higher_is_better": False,
+        "dtype": "f32 AlgFAC / f64 refinement" if prec else "f64",
         "data": "synthetic",
         "config": {"workload": desc, "n": n, "nnz": int(len(w["col"])), "nsub": int(w["nsub"]), "nrhs": nrhs,
                    "l2_policy": "inputs larger than L2"},
@@ -434,7 +443,7 @@ def main():
     ap.add_argument("--n", type=int, default=128,
                     help="grid edge (default 128, the benchmark workload; smaller edges "
                          "are for profiling captures only)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "kappa3d_256", "batched_64"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "kappa3d_256", "batched_64", "aniso2d_512"],
                     help="poisson3d_128 (default, the headline) or one of the two larger "
                          "mixed-precision configurations, printed as a line of their own")
     ap.add_argument("--no-autotune", action="store_true",

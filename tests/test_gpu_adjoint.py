@@ -89,11 +89,34 @@ def test_gradient_matches_central_differences_32_coefficients():
     assert np.isclose(fdb, gb @ d, rtol=1e-6)
 
 
-def test_lognormal_96_gradient_sampled():
+def _refined_loss(s, rp_d, ci_d, v_np, b_d, xt_d, tol):
+    """Loss of the solve of a perturbed matrix (same sparsity, values v_np):
+    x += AMG-DD correction of b - A' x with the unperturbed handle s (its
+    restriction and FAC launch), the residual with A' from the handle-free
+    residual entry point, until ||b - A' x|| <= tol ||b||."""
+    n = b_d.numel()
+    v_d = torch.from_numpy(v_np).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r_all = torch.zeros(int(s.offsets[-1]), dtype=torch.float64, device="cuda")
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bn = float(torch.linalg.vector_norm(b_d))
+    for _ in range(300):
+        capi.amgdd_residual_csr_noalloc(n, rp_d, ci_d, v_d, b_d, x, r_all[:n], nrm)
+        if float(nrm[0]) ** 0.5 <= tol * bn:
+            return 0.5 * float(torch.sum((x - xt_d) ** 2))
+        capi.amgdd_restrict(s.h, r_all)
+        capi.amgdd_fac(s.h, r_all, x)
+    raise AssertionError("refinement did not converge")
+
+
+def test_lognormal_96_gradient_32_coefficients():
     """96^3 diffusion with kappa = exp(g), g a Gaussian random field (length
     0.1, variance 1), loss 1/2 ||x - x_t||^2, 216 subdomains of 16^3, padding
     2: the GPU gradient equals the oracle's (same solves) on every node, and
-    central differences agree on sampled coefficients."""
+    central differences (h = 1e-6) agree on 32 random coefficients. Each
+    perturbed loss solves A(kappa +- h e_m) x = b to 1e-13 by refinement
+    with the unperturbed AMG-DD hierarchy."""
+    from paper_1906_10575_gb300 import Solver
     n = 96
     kappa = I.lognormal_kappa(n, seed=0)
     b = I.uniform_rhs(n ** 3, 1)
@@ -107,12 +130,19 @@ def test_lognormal_96_gradient_sampled():
     assert np.array_equal(x, xo) and np.array_equal(gb, lo)
     ref = kappa_gradient(kappa, xo, lo)
     assert np.allclose(gk, ref, rtol=1e-12, atol=1e-14 * abs(ref).max())
+    del o
+    s = Solver(rp, ci, v, part, nsub, 2, n_fac=2)
+    rp_d, ci_d = torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda()
+    b_d, xt_d = torch.from_numpy(b).cuda(), torch.from_numpy(xt).cuda()
     rng = np.random.default_rng(3)
-    for m in rng.choice(n ** 3, size=4, replace=False):
+    for m in rng.choice(n ** 3, size=32, replace=False):
         kp = kappa.copy().reshape(-1)
         km = kappa.copy().reshape(-1)
         kp[m] += 1e-6
         km[m] -= 1e-6
-        fd = (_loss(kp.reshape(kappa.shape), b, xt, (16, 16, 16), 1e-13)
-              - _loss(km.reshape(kappa.shape), b, xt, (16, 16, 16), 1e-13)) / 2e-6
+        vp = I.diffusion3d(kp.reshape(kappa.shape))[2]
+        vm = I.diffusion3d(km.reshape(kappa.shape))[2]
+        fd = (_refined_loss(s, rp_d, ci_d, vp, b_d, xt_d, 1e-13)
+              - _refined_loss(s, rp_d, ci_d, vm, b_d, xt_d, 1e-13)) / 2e-6
         assert abs(fd - gk[m]) <= 1e-5 * abs(gk[m]) + 1e-7 * abs(gk).max(), (m, fd, gk[m])
+    s.close()

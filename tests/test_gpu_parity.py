@@ -51,6 +51,10 @@ def _case(name):
         rp, ci, v = I.poisson2d(40, 40)
         part, nsub = I.box_partition((40, 40), (10, 10))
         return rp, ci, v, part, nsub, 0, I.uniform_rhs(1600, 5)
+    if name == "aniso2d":    # rotated anisotropic diffusion (theta = 3 pi / 16, eps = 1e-3), 9-point
+        rp, ci, v = I.rotated_anisotropic2d(48, 40)
+        part, nsub = I.box_partition((48, 40), (12, 10))
+        return rp, ci, v, part, nsub, 2, I.uniform_rhs(48 * 40, 7)
     if name == "batch3":     # three independent systems, block diagonal, uneven boxes
         rp, ci, v, part, nsub, B, picks, offs = I.batched_poisson(3, edges=(12, 16, 20), box=8, nrhs=1, seed=5)
         return rp, ci, v, part, nsub, 2, B[:, 0].copy()
@@ -61,7 +65,7 @@ def _case(name):
     raise KeyError(name)
 
 
-CASES = ["poisson2d_64", "ragged2d", "poisson3d_24", "kappa3d", "one_grid", "eta0", "single_level"]
+CASES = ["poisson2d_64", "ragged2d", "poisson3d_24", "kappa3d", "one_grid", "eta0", "single_level", "aniso2d"]
 
 
 @pytest.fixture(scope="module", params=CASES)
@@ -288,7 +292,7 @@ def test_fac_multi_equals_oracle_corrections(case, precision):
     s.close()
 
 
-@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d", "ragged2d"])
+@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d", "ragged2d", "aniso2d"])
 def test_hybrid_amgdd_bit_exact(case):
     """Hybrid AMG-DD (Algorithm 3) on every switch level equals the oracle's
     hybrid cycle; switching on the coarsest level is the plain V-cycle."""

@@ -89,3 +89,28 @@ def test_batched_poisson_is_block_diagonal():
     assert nsub == sub0 == part.max() + 1
     again = I.batched_poisson(5, edges=(8, 12, 20), box=8, nrhs=4, seed=11)
     assert np.array_equal(again[5], B) and again[6] == picks
+
+
+def test_rotated_anisotropic_stencil():
+    """9-point stencil of -div(K grad u), K = Q diag(1, eps) Q^T: symmetric,
+    positive definite, interior rows sum to zero; theta = 0, eps = 1 is the
+    5-point Laplacian (the mixed-derivative entries vanish); the stencil of an
+    interior node carries the rotated tensor's entries."""
+    import scipy.sparse as sp
+    th, eps = 3 * np.pi / 16, 1e-3
+    rp, ci, v = I.rotated_anisotropic2d(11, 9, th, eps)
+    A = sp.csr_matrix((v, ci, rp)).toarray()
+    assert np.array_equal(A, A.T) and np.linalg.eigvalsh(A).min() > 0
+    c, s = np.cos(th), np.sin(th)
+    K = np.array([[c, -s], [s, c]]) @ np.diag([1.0, eps]) @ np.array([[c, s], [-s, c]])
+    i = 4 * 11 + 5                        # interior node (x = 5, y = 4)
+    row = {j - i: A[i, j] for j in np.nonzero(A[i])[0]}
+    assert np.isclose(row[0], 2 * K[0, 0] + 2 * K[1, 1]) and abs(sum(row.values())) < 1e-14
+    assert np.isclose(row[1], -K[0, 0]) and np.isclose(row[-1], -K[0, 0])
+    assert np.isclose(row[11], -K[1, 1]) and np.isclose(row[-11], -K[1, 1])
+    assert np.isclose(row[12], -K[0, 1] / 2) and np.isclose(row[-12], -K[0, 1] / 2)
+    assert np.isclose(row[10], K[0, 1] / 2) and np.isclose(row[-10], K[0, 1] / 2)
+    rp0, ci0, v0 = I.rotated_anisotropic2d(7, 5, 0.0, 1.0)
+    A0 = sp.csr_matrix((v0, ci0, rp0)).toarray()
+    r5, c5, v5 = I.poisson2d(7, 5)
+    assert np.array_equal(A0, sp.csr_matrix((v5, c5, r5)).toarray())

@@ -48,6 +48,7 @@ CASES = [
     ("3d24_eta2", lambda: (*I.poisson3d(24, 24, 24), *I.box_partition((24, 24, 24), (8, 8, 8)), 2)),
     ("3d_kappa", lambda: (*I.diffusion3d(I.checkerboard_kappa(20, 4, 3)),
                           *I.box_partition((20, 20, 20), (10, 10, 5)), [2, 1])),
+    ("2d_aniso", lambda: (*I.rotated_anisotropic2d(40, 36), *I.box_partition((40, 36), (10, 9)), 2)),
 ]
 
 

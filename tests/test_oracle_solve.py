@@ -42,10 +42,20 @@ def test_residual_and_restriction_match_scipy():
         assert np.allclose(rl[l + 1], o.scipy(l, "R") @ rl[l], rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("kind,eta,nfac", [("2d", 1, 2), ("2d", 2, 3), ("3d", 1, 2), ("3d", 2, 1)])
+def _aniso(nx, ny, box, eta, seed=0):
+    rp, ci, v = I.rotated_anisotropic2d(nx, ny)
+    part, nsub = I.box_partition((nx, ny), box)
+    o = Oracle(rp, ci, v, part, nsub, eta)
+    return o, sp.csr_matrix((v, ci, rp)), I.uniform_rhs(nx * ny, seed)
+
+
+@pytest.mark.parametrize("kind,eta,nfac", [("2d", 1, 2), ("2d", 2, 3), ("3d", 1, 2), ("3d", 2, 1),
+                                           ("aniso", 2, 2)])
 def test_algfac_equals_masked_global_cycle(kind, eta, nfac):
     if kind == "2d":
         o, A, b = _problem2d(40, 36, (10, 9), eta)
+    elif kind == "aniso":   # 9-point rotated anisotropy: positive off-diagonals, long-range coarse stencils
+        o, A, b = _aniso(40, 36, (10, 9), eta)
     else:
         o, A, b = _problem3d(16, 8, eta)
     assert o.violations() == 0
@@ -115,6 +125,10 @@ def test_converged_solutions_match_dense_solve():
     xd = np.linalg.solve(A3.toarray(), b3)
     xa, ha = o3.amgdd_solve(b3, 2, tol=1e-12)
     assert np.linalg.norm(xa - xd) <= 1e-9 * np.linalg.norm(xd)
+    oa, Aa, ba = _aniso(24, 20, (8, 10), 2, seed=4)
+    xd = np.linalg.solve(Aa.toarray(), ba)
+    for x, h in (oa.amgdd_solve(ba, 2, tol=1e-12, maxit=400), oa.vcycle_solve(ba, tol=1e-12, maxit=800)):
+        assert h[-1] <= 1e-12 and np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
 
 
 def test_amgdd_history_definition():

@@ -413,7 +413,8 @@ def run_extra(args, name, stream, dist, local):
         "iterations": it, "final_relres": info["final_relres"],
         "vcycle_fp64": {"ms_all_columns": round(v_ms, 3), "iterations": v_it},
         "amgdd_over_vcycle_time": round(ms / v_ms, 3),
-        "fac": {"kernel": "k_fac_all_grids_r" if multi else "k_fac_all_grids", "ms_per_launch": round(fac_ms, 3),
+        "fac": {"kernel": _fac_kernel(tune["best_candidate"] if tune else (None if not multi else 9)),
+                "candidate": tune["best_candidate"] if tune else None, "ms_per_launch": round(fac_ms, 3),
                 "algorithmic_bytes": fac_b, "achieved_gbs": round(fac_gbs, 1), "peak_gbs": hbm,
                 "hbm_frac": round(fac_gbs / hbm, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
         "composite_overhead": round(st.composite_overhead, 3), "levels": st.num_levels,

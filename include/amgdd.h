@@ -287,9 +287,14 @@ amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32
  *               19: g = 32 on every level. These two REORDER each row sum:
  *               results then differ from the other candidates by rounding
  *               (they need 16-bit local columns).
+ *   k = 20, 21: as 15 with the operator entries 2 (20) or 4 (21) steps ahead
+ *               prefetched into L1 instead of L2 (16-bit local columns).
+ *   k = 22..24: as 15, and every pass whose gathered level vector fits 16,
+ *               32 or 44 KB copies it to shared memory first (16-bit local
+ *               columns).
  * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
-#define AMGDD_FAC_CANDIDATES 20
-/* amgdd_autotune flags: also time candidates 18 and 19 */
+#define AMGDD_FAC_CANDIDATES 25
+/* amgdd_autotune flags: also time candidates 18 and 19 (reordered row sums) */
 #define AMGDD_TUNE_ALLOW_REORDERED 1
 
 /* Uses candidate k for the FAC step of nrhs (1, 2 or 4) columns from now on.

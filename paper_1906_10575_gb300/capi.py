@@ -66,7 +66,7 @@ EXPORTS = [
     "amgdd_set_fac_kernel", "amgdd_autotune",
 ]
 
-FAC_CANDIDATES = 20
+FAC_CANDIDATES = 25
 TUNE_ALLOW_REORDERED = 1
 
 _lib = None

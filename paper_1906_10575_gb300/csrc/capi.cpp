@@ -919,6 +919,7 @@ static cudaError_t launch_candidate(amgdd_handle h, FacParams P, int nrhs, int k
         return launch_fac_all_grids(P, P.nsub, h->threads, st);
     }
     if (k < 18) return launch_fac_multi(P, P.nsub, nrhs, k - 8, st);
+    if (k >= 20) return launch_fac_multi(P, P.nsub, nrhs, k - 9, st);   // variants 11-15
     for (int l = 0; l <= kMaxLevels; ++l) P.grp[l] = k == 18 ? h->grp_level[l] : (int8_t)32;
     return launch_fac_multi(P, P.nsub, nrhs, 10, st);
 }
@@ -1393,7 +1394,8 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
 // single-column kernel with schedule k + 1 (one column only; FP32 composite
 // grids have schedules 1 and 8), 9 <= k < 18 the several-column kernel's
 // variant k - 8, 18 and 19 its group-per-row variant (lanes per row by level
-// size, or 32 on every level), whose row sums are not the ascending chain.
+// size, or 32 on every level), whose row sums are not the ascending chain,
+// 20-24 its variants 11-15 (L1 prefetch, shared-memory staging).
 static bool candidate_applies(amgdd_handle h, int nrhs, int k)
 {
     if (k < 0 || k >= AMGDD_FAC_CANDIDATES) return false;
@@ -1402,7 +1404,7 @@ static bool candidate_applies(amgdd_handle h, int nrhs, int k)
     return true;
 }
 
-static bool candidate_reorders(int k) { return k >= 18; }
+static bool candidate_reorders(int k) { return k == 18 || k == 19; }
 
 static void drop_graphs(amgdd_handle h)
 {

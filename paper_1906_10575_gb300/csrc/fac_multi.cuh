@@ -42,19 +42,21 @@ __device__ __forceinline__ VecR<T, R> load_r(const T *__restrict__ p)
     return o;
 }
 
-// Hint that the line holding p is wanted soon: fetched into L2, no register
-// is held and nothing waits for it.
-__device__ __forceinline__ void prefetch_l2(const void *p)
+// Hint that the line holding p is wanted soon: fetched into L2 (or into L1
+// and L2), no register is held and nothing waits for it.
+template <bool TO_L1>
+__device__ __forceinline__ void prefetch_line(const void *p)
 {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    if constexpr (TO_L1) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    else asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // s_j = sum_k a_k x[c_k * R + j] for the lane's row, one fma chain per column.
 // UNR entries are loaded before any of them is used (UNR operator loads and
 // UNR gathers in flight per lane); the fmas stay in ascending entry order.
-// PF > 0: each step first asks L2 for the operator entries PF steps ahead, so
-// their loads find them there instead of in HBM (entries past the row's
-// length are not touched).
+// PF != 0: each step first asks L2 (PF > 0) or L1 (PF < 0) for the operator
+// entries |PF| steps ahead, so their loads find them there instead of in HBM
+// (entries past the row's length are not touched).
 template <class CI, class T, int R, int UNR, int PF = 0, class SV>
 __device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint16_t *rlen, const CI *col,
                                                  const SV *val, int64_t slice, int lane, int64_t row,
@@ -66,15 +68,16 @@ __device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint
 #pragma unroll
     for (int j = 0; j < R; ++j) s.v[j] = T(0);
     int k = 0;
-    if constexpr (PF > 0) {
+    if constexpr (PF != 0) {
+        constexpr int D = PF > 0 ? PF : -PF;
 #pragma unroll 1
         for (; k + UNR <= len; k += UNR) {
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                const int kp = k + PF * UNR + u;
+                const int kp = k + D * UNR + u;
                 if (kp < len) {
-                    prefetch_l2(col + base + 32 * kp);
-                    prefetch_l2(val + base + 32 * kp);
+                    prefetch_line<(PF < 0)>(col + base + 32 * kp);
+                    prefetch_line<(PF < 0)>(val + base + 32 * kp);
                 }
             }
             int c[UNR];
@@ -190,16 +193,37 @@ __device__ __forceinline__ void rows_dot(const Block &B, int g, const FacViewDev
     }
 }
 
-template <class CI, class T, int R, int UNR, int PF, bool GRP>
+// Shared-memory staging of a gathered vector: when the n values of the level
+// vector x fit the block's SB-byte buffer, the block copies them there and the
+// pass's gathers read the copy (the pass writes other vectors only, and the
+// previous pass ended at a barrier). Called by every thread of the block; the
+// condition is the same for all of them.
+template <int SB, class T>
+__device__ __forceinline__ const T *stage(const Block &B, const T *__restrict__ x, int64_t n, unsigned char *buf)
+{
+    if constexpr (SB > 0) {
+        if (n * (int64_t)sizeof(T) <= SB) {
+            T *sb = reinterpret_cast<T *>(buf);
+            for (int64_t i = B.tid; i < n; i += B.nt) sb[i] = x[i];
+            __syncthreads();
+            return sb;
+        }
+    }
+    return x;
+}
+
+template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB>
 __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B, const FacLevelDesc &d, int g,
-                                             const FacViewDev &V, int64_t s0, int first, int r0, int r1)
+                                             const FacViewDev &V, int64_t s0, int first, int r0, int r1,
+                                             unsigned char *buf)
 {
     T *__restrict__ u = static_cast<T *>(P.u) + d.row0 * R;
     T *__restrict__ t = static_cast<T *>(P.t) + d.row0 * R;
     T *__restrict__ dd = static_cast<T *>(P.d) + d.row0 * R;
     const T *__restrict__ f = static_cast<const T *>(P.f) + d.row0 * R;
     const T *__restrict__ l1 = static_cast<const T *>(P.l1inv) + d.row0;
-    rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, u, [&](int r, const VecR<T, R> &s) {
+    const T *ux = stage<SB>(B, u, (int64_t)d.nBar * R, buf);
+    rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, ux, [&](int r, const VecR<T, R> &s) {
 #pragma unroll
         for (int j = 0; j < R; ++j) dd[r * R + j] = (f[r * R + j] - s.v[j]) * l1[r];
     });
@@ -215,9 +239,10 @@ __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B,
     __syncthreads();
 }
 
-template <class CI, class T, int R, int UNR, int MINB, int PF, bool GRP>
+template <class CI, class T, int R, int UNR, int MINB, int PF, bool GRP, int SB>
 __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
 {
+    extern __shared__ __align__(16) unsigned char fac_stage[];
     Block B;
     B.tid = threadIdx.x;
     B.nt = blockDim.x;
@@ -290,15 +315,15 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                         }
                     }
                     __syncthreads();
-                    relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, fac_stage);
                 } else {
-                    relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC);
-                    relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC, fac_stage);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal, fac_stage);
                 }
                 {
-                    const T *__restrict__ t = Pt + d.row0 * R;
                     const T *__restrict__ s = Ps + d.row0 * R;
                     T *__restrict__ w = Pw + d.row0 * R;
+                    const T *t = stage<SB>(B, Pt + d.row0 * R, (int64_t)d.nBar * R, fac_stage);
                     rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.At, d.sAt, d.row0, 0, 0, d.nBar, t,
                                                      [&](int r, const VecR<T, R> &at) {
 #pragma unroll
@@ -307,7 +332,7 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                 }
                 __syncthreads();
                 {
-                    const T *__restrict__ w = Pw + d.row0 * R;
+                    const T *w = stage<SB>(B, Pw + d.row0 * R, (int64_t)d.nBar * R, fac_stage);
                     T *__restrict__ s1 = Ps + dn.row0 * R;
                     T *__restrict__ f1 = Pf + dn.row0 * R;
                     const T *__restrict__ u1 = Pu + dn.row0 * R;
@@ -382,7 +407,7 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                 const FacLevelDesc d = D[l];
                 const FacLevelDesc dn = D[l + 1];
                 T *__restrict__ u = Pu + d.row0 * R;
-                const T *__restrict__ u1 = Pu + dn.row0 * R;
+                const T *u1 = stage<SB>(B, Pu + dn.row0 * R, (int64_t)dn.nBar * R, fac_stage);
                 const int gl = GRP ? P.grp[l] : 1;
                 rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.P, d.sP, d.row0, 0, 0, d.nBar, u1,
                                                  [&](int r, const VecR<T, R> &pu) {
@@ -390,8 +415,8 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                     for (int j = 0; j < R; ++j) u[r * R + j] = u[r * R + j] + pu.v[j];
                 });
                 __syncthreads();
-                relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal);
-                relax_pass_r<CI, T, R, UNR, PF, GRP>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC);
+                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal, fac_stage);
+                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC, fac_stage);
             }
         }
 
@@ -417,20 +442,25 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
 //   9: UNR 2, 4 blocks, PF 4
 //  10: UNR 2, 3 blocks, PF 2, with g lanes per row on level l where
 //      P.grp[l] = g > 1
+//  11: UNR 2, 4 blocks, 2 steps ahead into L1   12: same, 4 steps ahead
+//  13-15: as 7, with gathered level vectors of up to 16, 32 or 44 KB staged
+//      in shared memory (with the block's static shared memory, the total
+//      stays within the 48 KB a launch gets without an opt-in attribute)
 // 32-bit local columns (composite levels above 65,535 points) use variant 1.
-constexpr int kMultiVariants = 10;
+constexpr int kMultiVariants = 15;
 
-template <class CI, class T, int R, int UNR, int MINB, int PF = 0, bool GRP = false>
+template <class CI, class T, int R, int UNR, int MINB, int PF = 0, bool GRP = false, int SB = 0>
 cudaError_t launch_fac_r_variant(const FacParams &P, int nsub, cudaStream_t st)
 {
-    auto kern = dev::k_fac_all_grids_r<CI, T, R, UNR, MINB, PF, GRP>;
+    static_assert(SB % 16 == 0 && SB <= 44 * 1024, "staging buffer plus static shared memory within 48 KB");
+    auto kern = dev::k_fac_all_grids_r<CI, T, R, UNR, MINB, PF, GRP, SB>;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, SB);
     if (e != cudaSuccess) return e;
     int ctas = (per_sm < 1 ? 1 : per_sm) * P.nbins;
     if (ctas > nsub) ctas = nsub;
     if ((e = cudaMemsetAsync(P.ctr, 0, sizeof(int32_t) * (size_t)P.nbins, st)) != cudaSuccess) return e;
-    kern<<<ctas, 512, 0, st>>>(P);
+    kern<<<ctas, 512, SB, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -448,6 +478,11 @@ cudaError_t launch_fac_r_typed(const FacParams &P, int nsub, int variant, cudaSt
     case 8: return launch_fac_r_variant<uint16_t, T, R, 2, 3, 2>(P, nsub, st);
     case 9: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 4>(P, nsub, st);
     case 10: return launch_fac_r_variant<uint16_t, T, R, 2, 3, 2, true>(P, nsub, st);
+    case 11: return launch_fac_r_variant<uint16_t, T, R, 2, 4, -2>(P, nsub, st);
+    case 12: return launch_fac_r_variant<uint16_t, T, R, 2, 4, -4>(P, nsub, st);
+    case 13: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 2, false, 16384>(P, nsub, st);
+    case 14: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 2, false, 32768>(P, nsub, st);
+    case 15: return launch_fac_r_variant<uint16_t, T, R, 2, 4, 2, false, 45056>(P, nsub, st);
     default: return launch_fac_r_variant<uint16_t, T, R, 1, 2>(P, nsub, st);
     }
 }

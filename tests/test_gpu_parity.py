@@ -333,21 +333,22 @@ def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
     ref = [step(Bh[:, j], np.zeros(n), 2) for j in range(4)]
     b = _dev(Bh[:, 0])
     single = [0, 7] if precision else list(range(9))
-    for k in single + list(range(9, 18)):    # 18, 19 reorder row sums: tested below
+    exact = single + list(range(9, 18)) + list(range(20, 25))    # 18, 19 reorder row sums: tested below
+    for k in exact:
         capi.amgdd_set_fac_kernel(s.h, 1, k)
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         capi.amgdd_iterate(s.h, b, x)
         assert np.array_equal(_host(x), ref[0]), k
     for nrhs in (2, 4):
         B = torch.from_numpy(np.ascontiguousarray(Bh[:, :nrhs])).cuda()
-        for k in range(9, 18):
+        for k in list(range(9, 18)) + list(range(20, 25)):
             capi.amgdd_set_fac_kernel(s.h, nrhs, k)
             X = torch.zeros((n, nrhs), dtype=torch.float64, device="cuda")
             capi.amgdd_iterate_multi(s.h, B, X)
             Xh = _host(X)
             for j in range(nrhs):
                 assert np.array_equal(Xh[:, j], ref[j]), (nrhs, k, j)
-    for k in ([1, 2, 3, 4, 5, 6, 8] if precision else []) + [20, -1]:
+    for k in ([1, 2, 3, 4, 5, 6, 8] if precision else []) + [25, -1]:
         with pytest.raises(capi.AmgddError):
             capi.amgdd_set_fac_kernel(s.h, 1, k)
     with pytest.raises(capi.AmgddError):
@@ -356,7 +357,8 @@ def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
         best, ms = capi.amgdd_autotune(s.h, nrhs, reps=2)
         applies = ms >= 0
         assert applies[best] and ms[best] == ms[applies].min()
-        assert applies[9:18].all() and not applies[18:].any() and (applies[:9].any() == (nrhs == 1))
+        assert applies[9:18].all() and applies[20:].all() and not applies[18:20].any()
+        assert applies[:9].any() == (nrhs == 1)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     info = s.solve(b, x, tol=1e-8, max_iter=100)
     xo = np.zeros(n)

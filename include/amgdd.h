@@ -306,7 +306,8 @@ amgdd_status amgdd_set_fac_kernel(amgdd_handle h, int32_t nrhs, int32_t candidat
  * that applies to nrhs (1, 2 or 4) columns on this handle's composite grids
  * (zero restricted residuals, a scratch solution allocated and freed here),
  * with CUDA events on `stream`, and keeps the fastest as amgdd_set_fac_kernel
- * would. Candidates that reorder row sums take part only with flags &
+ * would (candidates within 1 % of the fastest count as ties, which go to the
+ * lowest-numbered one). Candidates that reorder row sums take part only with flags &
  * AMGDD_TUNE_ALLOW_REORDERED. ms (HOST, may be NULL): AMGDD_FAC_CANDIDATES
  * doubles, the mean milliseconds per launch, -1 where a candidate does not
  * apply or was not timed. best (may be NULL): the chosen candidate.

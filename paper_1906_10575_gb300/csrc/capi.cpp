@@ -1466,6 +1466,8 @@ amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, int32_t 
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     int bk = -1;
     double bms = 0.0;
+    double times[AMGDD_FAC_CANDIDATES];
+    for (double &t : times) t = -1.0;
     for (int k = 0; k < AMGDD_FAC_CANDIDATES && e == cudaSuccess; ++k) {
         if (ms) ms[k] = -1.0;
         if (!candidate_applies(h, nrhs, k)) continue;
@@ -1481,12 +1483,21 @@ amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, int32_t 
         if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
         const double per = (double)t / reps;
         if (ms) ms[k] = per;
+        times[k] = per;
         if (bk < 0 || per < bms) {
             bk = k;
             bms = per;
         }
         h->launches += 1 + reps;
     }
+    // candidates within 1 % of the fastest are ties: keep the lowest-numbered,
+    // so repeated tuning of the same workload settles on the same kernel
+    if (e == cudaSuccess && bk >= 0)
+        for (int k = 0; k < bk; ++k)
+            if (times[k] >= 0.0 && times[k] <= 1.01 * bms) {
+                bk = k;
+                break;
+            }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(xs);

@@ -356,7 +356,8 @@ def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
     for nrhs in (1, 4):
         best, ms = capi.amgdd_autotune(s.h, nrhs, reps=2)
         applies = ms >= 0
-        assert applies[best] and ms[best] == ms[applies].min()
+        assert applies[best] and ms[best] <= 1.01 * ms[applies].min()
+        assert not (applies[:best] & (ms[:best] <= 1.01 * ms[applies].min())).any()
         assert applies[9:18].all() and applies[20:].all() and not applies[18:20].any()
         assert applies[:9].any() == (nrhs == 1)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -411,5 +412,5 @@ def test_group_per_row_candidates_within_tolerance(case, precision):
             assert np.all(np.abs(info["history"] - ho) <= 1e-10), k
             assert np.allclose(info["history"], ho, rtol=1e-4, atol=0), k
     best, ms = capi.amgdd_autotune(s.h, 1, reps=2, allow_reordered=True)
-    assert ms[18] > 0 and ms[19] > 0 and ms[best] == ms[ms >= 0].min()
+    assert ms[18] > 0 and ms[19] > 0 and ms[best] <= 1.01 * ms[ms >= 0].min()
     s.close()

@@ -207,7 +207,7 @@ def run_reference(args, w):
     """CPU oracle arm: each step is one AMG-DD iteration on all host cores."""
     from oracle import Oracle
     cores = os.cpu_count()
-    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"])
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], interp=args.interp)
     b = w["b"]
     # iterations to 1e-8 (identical on every implementation of the same arithmetic)
     t0 = time.perf_counter()
@@ -228,7 +228,7 @@ def run_reference(args, w):
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(per_iter, 3), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(w),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(_config(w), interp=args.interp),
         "iterations": iters, "full_solve_ms": round(full, 1),
         "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": cores, "kind": "oracle",
                          "sample": "one AMG-DD iteration over all 512 composite grids per step "
@@ -250,13 +250,13 @@ def max_over_ranks(values, dist=None):
     return [float(v) for v in t.cpu()]
 
 
-def cpu_baseline(w, iters):
+def cpu_baseline(w, iters, interp="direct"):
     """Oracle timed on a bounded sample: one full AMG-DD iteration (residual,
     restriction and AlgFAC on every composite grid, OpenMP over grids), scaled
     by the iterations to 1e-8."""
     from oracle import Oracle
     cores = os.cpu_count()
-    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"])
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], interp=interp)
     b = w["b"]
     t0 = time.perf_counter()
     o.amgdd_iteration(b, np.zeros(o.n), w["n_fac"])
@@ -302,7 +302,7 @@ def run_extra(args, name, stream, dist, local):
     prec = int(w.get("precision", 0))
     maxit = 2000
     t0 = time.perf_counter()
-    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
                precision=prec, schedule=args.schedule, stream=stream,
                max_coarse=16 * (len(w["edges"]) if multi else 1))
     setup_s = time.perf_counter() - t0
@@ -381,7 +381,7 @@ def run_extra(args, name, stream, dist, local):
     err = None
     if not multi and prec == 1 and not args.no_fp64_check:
         # FP64 AMG-DD on the same problem: reference solution for the error
-        s64 = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+        s64 = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
                      stream=stream)
         x64 = torch.zeros(n, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
@@ -409,7 +409,7 @@ def run_extra(args, name, stream, dist, local):
         "dtype": "f32 AlgFAC / f64 refinement" if prec else "f64",
         "data": "synthetic",
         "config": {"workload": desc, "n": n, "nnz": int(len(w["col"])), "nsub": int(w["nsub"]), "nrhs": nrhs,
-                   "l2_policy": "inputs larger than L2"},
+                   "l2_policy": "inputs larger than L2", "interp": args.interp},
         "iterations": it, "final_relres": info["final_relres"],
         "vcycle_fp64": {"ms_all_columns": round(v_ms, 3), "iterations": v_it},
         "amgdd_over_vcycle_time": round(ms / v_ms, 3),
@@ -450,6 +450,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FAC kernel instead of timing every candidate and "
                          "keeping the fastest")
+    ap.add_argument("--interp", default="direct", choices=["direct", "exti"],
+                    help="interpolation of the hierarchy: direct (default) or extended+i, "
+                         "truncated to 4 entries per row")
     ap.add_argument("--candidate", type=int, default=-1,
                     help="use this FAC kernel candidate instead of autotuning (profiling captures)")
     ap.add_argument("--nsys", type=int, default=64,
@@ -487,7 +490,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
-    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
                schedule=args.schedule, stream=stream)
     st = s.stats
     b = torch.from_numpy(w["b"]).cuda()
@@ -571,7 +574,7 @@ def main():
     mixed = None
     if not args.no_mixed:
         s.close()
-        sm = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+        sm = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
                     precision=1, stream=stream)
         cand_m = None
         if not args.no_autotune:
@@ -618,7 +621,7 @@ def main():
     # cycle on level --hybrid-level
     hybrid = None
     if args.hybrid_level > 0:
-        sh = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+        sh = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
                     hybrid_level=args.hybrid_level, stream=stream)
         with torch.cuda.stream(stream):
             timed(sh.hybrid_solve, args.warmup)
@@ -632,7 +635,7 @@ def main():
     # entry feeds four fma chains
     multi = None
     if not args.no_multi:
-        sq = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+        sq = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
                     stream=stream)
         Bm = torch.from_numpy(np.ascontiguousarray(np.stack([I.uniform_rhs(sq.n, j) for j in range(4)], 1))).cuda()
         Xm = torch.zeros_like(Bm)
@@ -707,7 +710,7 @@ def main():
         "metric": METRIC, "value": round(ms_dd, 3), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_dd, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(w),
+        "data": "synthetic", "config": dict(_config(w), interp=args.interp),
         "iterations": it_dd, "final_relres": i_dd[-1]["final_relres"],
         "gbs": round(dd_bytes / (ms_dd * 1e-3) / 1e9, 1),
         "vcycle": {"ms": round(ms_v, 3), "iterations": it_v, "final_relres": i_v[-1]["final_relres"],
@@ -728,7 +731,7 @@ def main():
         "hybrid": hybrid,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, it_dd)
+        line["cpu_baseline"] = cpu_baseline(w, it_dd, args.interp)
     if rank == 0:
         print(json.dumps(line))
     if s.h:

@@ -89,7 +89,16 @@ typedef struct {
                                (Algorithm 3, amg_hybrid_cycle / amg_hybrid_solve);
                                subdomains on level Lt are inherited from the
                                partition through the C points (FP64) */
-    int32_t reserved[5];
+    int32_t interp;         /* interpolation (Section 2; the paper uses hypre
+                               defaults it does not restate): 0 = direct over
+                               strong C neighbours (default); 1 = extended+i
+                               (distance two: strong C neighbours plus those
+                               of strong F neighbours, with the "+i" term and
+                               weak connections lumped into the diagonal) */
+    int32_t p_max;          /* extended+i only: keep the p_max largest |weights|
+                               per row, rescaled to the row's sum (0 = keep
+                               all; default 4) */
+    int32_t reserved[3];
 } amgdd_options;
 
 /* Statistics of a completed setup. */

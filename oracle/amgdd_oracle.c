@@ -29,7 +29,9 @@
  *     the smallest index; points with no strong connection in either
  *     direction become F points with an empty interpolation row;
  *   - interpolation: direct interpolation over strong C neighbours with
- *     positive off-diagonals lumped into the diagonal;
+ *     positive off-diagonals lumped into the diagonal; or (interp = 1) the
+ *     extended+i interpolation of the hypre defaults the paper names, with
+ *     truncation to pmax entries per row (exti_interp below);
  *   - smoother: CF l1-Jacobi, l1_i = sum_j |a_ij| over the whole row,
  *     delta_i = (f_i - (A u)_i) * (1 / l1_i); pre-smoothing C then F points,
  *     post-smoothing F then C points;
@@ -280,6 +282,199 @@ static void direct_interp(const Mat *A, const int64_t *srp, const int *sci, cons
     }
 }
 
+/* Extended+i interpolation (the distance-two interpolation of the hypre
+ * defaults that Section 6 names; the paper does not restate it, this follows
+ * its published definition). For an F point i with strong influencers S_i:
+ *   C_i = S_i n C, F_i = S_i n F (ascending),
+ *   Chat_i = C_i u (union over k in F_i of S_k n C), ascending;
+ *   abar_kl = a_kl if a_kl * a_kk < 0, else 0;
+ *   D_k = sum over l in Chat_i u {i} of abar_kl (row k ascending), k in F_i;
+ *   d   = a_ii + sum over the other entries n of row i (ascending) of
+ *           (a_in * abar_ni) / D_n   if n in F_i and D_n != 0,
+ *           a_in                     if n in F_i and D_n == 0,
+ *           a_in                     if n not in Chat_i u F_i,
+ *         nothing                    if n in Chat_i;
+ *   num_j = a_ij (0 if absent) + sum over k in F_i with D_k != 0 (ascending)
+ *           of (a_ik * abar_kj) / D_k,   j in Chat_i;
+ *   w_ij  = (-num_j) / d.
+ * Truncation (pmax > 0, rows with more than pmax entries): keep the pmax
+ * entries of largest |w| (ties to the smaller column), multiply them by
+ * (sum of all w, ascending) / (sum of the kept w, ascending) when the latter
+ * is nonzero, keep ascending columns. C points: injection; an F point with
+ * empty Chat_i: empty row. */
+static void exti_interp(const Mat *A, const int64_t *srp, const int *sci, const int *state,
+                        const int *cmap, int nc, int pmax, Mat *P)
+{
+    int n = A->n;
+    int *inC = xmalloc(sizeof(int) * (size_t)(n > 0 ? n : 1));   /* Chat membership: owner row */
+    int *inF = xmalloc(sizeof(int) * (size_t)(n > 0 ? n : 1));   /* F_i membership: owner row */
+    double *Dk = xmalloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) inC[i] = inF[i] = -1;
+    int64_t cap = 1024, used = 0;
+    int *rc = xmalloc(sizeof(int) * (size_t)cap);
+    double *rv = xmalloc(sizeof(double) * (size_t)cap);
+    int64_t *rp = xcalloc((size_t)n + 1, sizeof(int64_t));
+    int *ch = xmalloc(sizeof(int) * 64), chcap = 64;
+    double *wv = xmalloc(sizeof(double) * 64);
+    int *ord = xmalloc(sizeof(int) * 64);
+    for (int i = 0; i < n; ++i) {
+        int cnt = 0;
+        if (state[i] == 1) {
+            ch[0] = cmap[i];
+            wv[0] = 1.0;
+            cnt = 1;
+        } else {
+            /* Chat_i and F_i */
+            for (int64_t q = srp[i]; q < srp[i + 1]; ++q) {
+                int j = sci[q];
+                if (state[j] == 1) {
+                    if (inC[j] != i) {
+                        inC[j] = i;
+                        if (cnt == chcap) {
+                            chcap *= 2;
+                            ch = realloc(ch, sizeof(int) * (size_t)chcap);
+                            wv = realloc(wv, sizeof(double) * (size_t)chcap);
+                            ord = realloc(ord, sizeof(int) * (size_t)chcap);
+                        }
+                        ch[cnt++] = j;
+                    }
+                } else {
+                    inF[j] = i;
+                    for (int64_t q2 = srp[j]; q2 < srp[j + 1]; ++q2) {
+                        int m = sci[q2];
+                        if (state[m] == 1 && inC[m] != i) {
+                            inC[m] = i;
+                            if (cnt == chcap) {
+                                chcap *= 2;
+                                ch = realloc(ch, sizeof(int) * (size_t)chcap);
+                                wv = realloc(wv, sizeof(double) * (size_t)chcap);
+                                ord = realloc(ord, sizeof(int) * (size_t)chcap);
+                            }
+                            ch[cnt++] = m;
+                        }
+                    }
+                }
+            }
+            /* ascending Chat_i (insertion sort: the sets are small) */
+            for (int a = 1; a < cnt; ++a) {
+                int v = ch[a], b = a - 1;
+                while (b >= 0 && ch[b] > v) { ch[b + 1] = ch[b]; --b; }
+                ch[b + 1] = v;
+            }
+            if (cnt > 0) {
+                /* D_k for k in F_i */
+                for (int64_t q = srp[i]; q < srp[i + 1]; ++q) {
+                    int k = sci[q];
+                    if (inF[k] != i) continue;
+                    double akk = 0.0, D = 0.0;
+                    for (int64_t e = A->rp[k]; e < A->rp[k + 1]; ++e)
+                        if (A->ci[e] == k) akk = A->v[e];
+                    for (int64_t e = A->rp[k]; e < A->rp[k + 1]; ++e) {
+                        int l = A->ci[e];
+                        if (l != i && inC[l] != i) continue;
+                        double a = A->v[e];
+                        if (a * akk < 0.0) D = D + a;
+                    }
+                    Dk[k] = D;
+                }
+                /* d */
+                double d = 0.0;
+                for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e)
+                    if (A->ci[e] == i) d = A->v[e];
+                for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e) {
+                    int nn = A->ci[e];
+                    if (nn == i) continue;
+                    double a = A->v[e];
+                    if (inF[nn] == i) {
+                        if (Dk[nn] != 0.0) {
+                            double akk = 0.0, aki = 0.0;
+                            for (int64_t f = A->rp[nn]; f < A->rp[nn + 1]; ++f) {
+                                if (A->ci[f] == nn) akk = A->v[f];
+                                if (A->ci[f] == i) aki = A->v[f];
+                            }
+                            double abar = aki * akk < 0.0 ? aki : 0.0;
+                            d = d + (a * abar) / Dk[nn];
+                        } else {
+                            d = d + a;
+                        }
+                    } else if (inC[nn] != i) {
+                        d = d + a;
+                    }
+                }
+                /* num_j, w_ij */
+                for (int t = 0; t < cnt; ++t) {
+                    int j = ch[t];
+                    double num = 0.0;
+                    for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e)
+                        if (A->ci[e] == j) num = A->v[e];
+                    for (int64_t q = srp[i]; q < srp[i + 1]; ++q) {
+                        int k = sci[q];
+                        if (inF[k] != i || Dk[k] == 0.0) continue;
+                        double aik = 0.0, akk = 0.0, akj = 0.0;
+                        for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e)
+                            if (A->ci[e] == k) aik = A->v[e];
+                        for (int64_t f = A->rp[k]; f < A->rp[k + 1]; ++f) {
+                            if (A->ci[f] == k) akk = A->v[f];
+                            if (A->ci[f] == j) akj = A->v[f];
+                        }
+                        double abar = akj * akk < 0.0 ? akj : 0.0;
+                        num = num + (aik * abar) / Dk[k];
+                    }
+                    wv[t] = (-num) / d;
+                }
+                /* truncation */
+                if (pmax > 0 && cnt > pmax) {
+                    for (int t = 0; t < cnt; ++t) ord[t] = t;
+                    for (int a = 1; a < cnt; ++a) {   /* by |w| descending, then column */
+                        int v = ord[a], b = a - 1;
+                        while (b >= 0 && (fabs(wv[ord[b]]) < fabs(wv[v]) ||
+                                          (fabs(wv[ord[b]]) == fabs(wv[v]) && ch[ord[b]] > ch[v]))) {
+                            ord[b + 1] = ord[b];
+                            --b;
+                        }
+                        ord[b + 1] = v;
+                    }
+                    char keep[4096];
+                    char *kp = cnt <= 4096 ? keep : xmalloc((size_t)cnt);
+                    for (int t = 0; t < cnt; ++t) kp[t] = 0;
+                    for (int t = 0; t < pmax; ++t) kp[ord[t]] = 1;
+                    double all = 0.0, kept = 0.0;
+                    for (int t = 0; t < cnt; ++t) all = all + wv[t];
+                    for (int t = 0; t < cnt; ++t)
+                        if (kp[t]) kept = kept + wv[t];
+                    int o = 0;
+                    for (int t = 0; t < cnt; ++t) {
+                        if (!kp[t]) continue;
+                        ch[o] = ch[t];
+                        wv[o] = kept != 0.0 ? wv[t] * (all / kept) : wv[t];
+                        ++o;
+                    }
+                    if (kp != keep) free(kp);
+                    cnt = o;
+                }
+                for (int t = 0; t < cnt; ++t) ch[t] = cmap[ch[t]];
+            }
+        }
+        if (used + cnt > cap) {
+            while (used + cnt > cap) cap *= 2;
+            rc = realloc(rc, sizeof(int) * (size_t)cap);
+            rv = realloc(rv, sizeof(double) * (size_t)cap);
+        }
+        for (int t = 0; t < cnt; ++t) {
+            rc[used + t] = ch[t];
+            rv[used + t] = wv[t];
+        }
+        used += cnt;
+        rp[i + 1] = used;
+    }
+    P->n = n;
+    P->m = nc;
+    P->rp = rp;
+    P->ci = rc;
+    P->v = rv;
+    free(inC); free(inF); free(Dk); free(ch); free(wv); free(ord);
+}
+
 /* R = P^T with ascending fine index in each row. */
 static void transpose(const Mat *P, Mat *R)
 {
@@ -431,7 +626,7 @@ static void mat_copy_in(Mat *M, int n, const int64_t *rp, const int *ci, const d
  * A_{l+1} = R_l A_l P_l until n_l <= max_coarse, max_levels levels exist, or
  * the split keeps more than 90% of the points (Section 2). */
 void *orc_hier_build(int n, const int64_t *rp, const int *ci, const double *v, double theta,
-                     int max_coarse, int max_levels)
+                     int max_coarse, int max_levels, int interp, int pmax)
 {
     Hier *H = xcalloc(1, sizeof(Hier));
     if (max_levels > ORC_MAXLEV) max_levels = ORC_MAXLEV;
@@ -458,7 +653,8 @@ void *orc_hier_build(int n, const int64_t *rp, const int *ci, const double *v, d
             cf[i] = (state[i] == 1);
             cmap[i] = cf[i] ? c++ : -1;
         }
-        direct_interp(A, srp, sci, state, cmap, nc, &H->P[l]);
+        if (interp == 1) exti_interp(A, srp, sci, state, cmap, nc, pmax, &H->P[l]);
+        else direct_interp(A, srp, sci, state, cmap, nc, &H->P[l]);
         transpose(&H->P[l], &H->R[l]);
         galerkin(&H->R[l], A, &H->P[l], &H->A[l + 1]);
         H->cf[l] = cf;

@@ -46,7 +46,8 @@ def oracle_lib():
         lib = C.CDLL(build_oracle())
         vp = C.c_void_p
         sig = {
-            "orc_hier_build": (vp, [C.c_int, i64p, i32p, f64p, C.c_double, C.c_int, C.c_int]),
+            "orc_hier_build": (vp, [C.c_int, i64p, i32p, f64p, C.c_double, C.c_int, C.c_int, C.c_int,
+                                    C.c_int]),
             "orc_hier_free": (None, [vp]),
             "orc_hier_status": (C.c_int, [vp]),
             "orc_hier_nlev": (C.c_int, [vp]),
@@ -102,7 +103,7 @@ class Oracle:
     """
 
     def __init__(self, rowptr, col, val, part=None, nsub=1, padding=1,
-                 theta=0.25, max_coarse=16, max_levels=25):
+                 theta=0.25, max_coarse=16, max_levels=25, interp="direct", pmax=4):
         lib = oracle_lib()
         self.lib = lib
         self.h = None
@@ -111,8 +112,10 @@ class Oracle:
         ci = np.ascontiguousarray(col, dtype=np.int32)
         v = _c64(val)
         self.n = len(rp) - 1
-        self.h = lib.orc_hier_build(self.n, rp, ci, v, float(theta),
-                                    int(max_coarse), int(max_levels))
+        if interp not in ("direct", "exti"):
+            raise ValueError("interp is 'direct' or 'exti' (extended+i)")
+        self.h = lib.orc_hier_build(self.n, rp, ci, v, float(theta), int(max_coarse), int(max_levels),
+                                    1 if interp == "exti" else 0, int(pmax))
         st = lib.orc_hier_status(self.h)
         if st != 0:
             lib.orc_hier_free(self.h)

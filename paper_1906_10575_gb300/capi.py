@@ -35,7 +35,8 @@ class amgdd_options(C.Structure):
     _fields_ = [("theta", C.c_double), ("max_coarse", C.c_int32), ("max_levels", C.c_int32),
                 ("n_fac", C.c_int32), ("strict_assumption", C.c_int32), ("host_only", C.c_int32),
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("precision", C.c_int32),
-                ("hybrid_level", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("hybrid_level", C.c_int32), ("interp", C.c_int32), ("p_max", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class amgdd_setup_stats(C.Structure):

@@ -39,6 +39,8 @@ struct HierarchyParams {
     double theta = 0.25;
     int max_coarse = 16;
     int max_levels = 25;
+    int interp = 0;       // 0 direct, 1 extended+i
+    int p_max = 4;        // extended+i truncation (0 = none)
 };
 
 // Returns an empty string on success, else the reason.

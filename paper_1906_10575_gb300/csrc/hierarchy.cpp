@@ -13,6 +13,8 @@
 //   * interp.   : F point i, strong C neighbours C_i, ascending sums
 //                 alpha = sum_{j != i, a_ij < 0} a_ij / sum_{k in C_i} a_ik,
 //                 d = a_ii + sum_{j != i, a_ij > 0} a_ij,  w_ik = (-alpha a_ik) / d;
+//   * ext.+i    : (option) distance-two interpolation; its sums and their
+//                 order are stated at extended_i_interpolation below;
 //   * Galerkin  : entry (I,J) of R A P sums (p_iI * a_ij) * p_jJ, fine i
 //                 ascending, then j ascending, then J; the pattern keeps every
 //                 structural term;
@@ -190,6 +192,127 @@ Csr direct_interpolation(const Csr &A, const Pattern &S, const std::vector<uint8
     return P;
 }
 
+// Entry (r, c) of A, 0 when it is not stored (columns ascend within a row).
+double entry_of(const Csr &A, int32_t r, int32_t c)
+{
+    const auto b = A.idx.begin() + A.ptr[r], e = A.idx.begin() + A.ptr[r + 1];
+    const auto it = std::lower_bound(b, e, c);
+    return (it != e && *it == c) ? A.val[(size_t)(it - A.idx.begin())] : 0.0;
+}
+
+// Extended+i interpolation. F point i, strong set S_i (ascending):
+//   F_i = strong F neighbours; H_i = strong C neighbours, and the strong C
+//   neighbours of every k in F_i, ascending;
+//   ab(k, l) = a_kl when a_kl and a_kk have opposite signs, else 0;
+//   D_k = sum of ab(k, l) over row k's entries l in H_i or l = i, ascending;
+//   d = a_ii, then over row i's other entries n ascending: n in F_i adds
+//       (a_in * ab(n, i)) / D_n (or a_in when D_n = 0); n outside H_i and F_i
+//       adds a_in; n in H_i adds nothing;
+//   num_j = a_ij (0 if absent), then for k in F_i ascending with D_k != 0:
+//       + (a_ik * ab(k, j)) / D_k;   w_ij = (-num_j) / d, j in H_i.
+// With p_max > 0 a row longer than p_max keeps its p_max largest |w| (the
+// smaller column first on equal |w|), scaled by sum(all w) / sum(kept w)
+// (ascending sums) when the kept sum is not zero. C points inject; an F point
+// with empty H_i has an empty row.
+Csr extended_i_interpolation(const Csr &A, const Pattern &S, const std::vector<uint8_t> &isC,
+                             const std::vector<int32_t> &coarse, int32_t nc, int p_max)
+{
+    const int32_t n = A.rows;
+    Csr P;
+    P.rows = n;
+    P.cols = nc;
+    P.ptr.assign((size_t)n + 1, 0);
+    std::vector<int32_t> tagH((size_t)n, -1), tagF((size_t)n, -1);
+    std::vector<double> D((size_t)n, 0.0);
+    std::vector<int32_t> H;
+    std::vector<double> w;
+    auto ab = [&](int32_t k, int32_t l) {
+        const double a = entry_of(A, k, l);
+        return a * entry_of(A, k, k) < 0.0 ? a : 0.0;
+    };
+    for (int32_t i = 0; i < n; ++i) {
+        if (isC[i]) {
+            P.idx.push_back(coarse[i]);
+            P.val.push_back(1.0);
+            P.ptr[i + 1] = (int64_t)P.idx.size();
+            continue;
+        }
+        H.clear();
+        for (int64_t q = S.ptr[i]; q < S.ptr[i + 1]; ++q) {
+            const int32_t j = S.idx[q];
+            if (isC[j]) {
+                if (tagH[j] != i) { tagH[j] = i; H.push_back(j); }
+                continue;
+            }
+            tagF[j] = i;
+            for (int64_t q2 = S.ptr[j]; q2 < S.ptr[j + 1]; ++q2) {
+                const int32_t m = S.idx[q2];
+                if (isC[m] && tagH[m] != i) { tagH[m] = i; H.push_back(m); }
+            }
+        }
+        if (H.empty()) {
+            P.ptr[i + 1] = (int64_t)P.idx.size();
+            continue;
+        }
+        std::sort(H.begin(), H.end());
+        for (int64_t q = S.ptr[i]; q < S.ptr[i + 1]; ++q) {
+            const int32_t k = S.idx[q];
+            if (tagF[k] != i) continue;
+            const double akk = entry_of(A, k, k);
+            double s = 0.0;
+            for (int64_t e = A.ptr[k]; e < A.ptr[k + 1]; ++e) {
+                const int32_t l = A.idx[e];
+                if (l == i || tagH[l] == i)
+                    if (A.val[e] * akk < 0.0) s = s + A.val[e];
+            }
+            D[k] = s;
+        }
+        double d = entry_of(A, i, i);
+        for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+            const int32_t nn = A.idx[e];
+            if (nn == i) continue;
+            if (tagF[nn] == i) d = D[nn] != 0.0 ? d + (A.val[e] * ab(nn, i)) / D[nn] : d + A.val[e];
+            else if (tagH[nn] != i) d = d + A.val[e];
+        }
+        w.assign(H.size(), 0.0);
+        for (size_t t = 0; t < H.size(); ++t) {
+            const int32_t j = H[t];
+            double num = entry_of(A, i, j);
+            for (int64_t q = S.ptr[i]; q < S.ptr[i + 1]; ++q) {
+                const int32_t k = S.idx[q];
+                if (tagF[k] != i || D[k] == 0.0) continue;
+                num = num + (entry_of(A, i, k) * ab(k, j)) / D[k];
+            }
+            w[t] = (-num) / d;
+        }
+        std::vector<uint8_t> keep(H.size(), 1);
+        if (p_max > 0 && (int)H.size() > p_max) {
+            std::vector<int32_t> byw(H.size());
+            std::iota(byw.begin(), byw.end(), 0);
+            std::sort(byw.begin(), byw.end(), [&](int32_t a, int32_t b) {
+                const double fa = std::fabs(w[a]), fb = std::fabs(w[b]);
+                return fa != fb ? fa > fb : H[a] < H[b];
+            });
+            std::fill(keep.begin(), keep.end(), 0);
+            for (int t = 0; t < p_max; ++t) keep[byw[t]] = 1;
+            double all = 0.0, kept = 0.0;
+            for (size_t t = 0; t < H.size(); ++t) all = all + w[t];
+            for (size_t t = 0; t < H.size(); ++t)
+                if (keep[t]) kept = kept + w[t];
+            if (kept != 0.0)
+                for (size_t t = 0; t < H.size(); ++t)
+                    if (keep[t]) w[t] = w[t] * (all / kept);
+        }
+        for (size_t t = 0; t < H.size(); ++t)
+            if (keep[t]) {
+                P.idx.push_back(coarse[H[t]]);
+                P.val.push_back(w[t]);
+            }
+        P.ptr[i + 1] = (int64_t)P.idx.size();
+    }
+    return P;
+}
+
 Csr transpose(const Csr &P)
 {
     Csr R;
@@ -314,7 +437,8 @@ std::string build_hierarchy(const Csr &A0, const HierarchyParams &prm, Hierarchy
         for (int32_t i = 0; i < cur.A.rows; ++i)
             if (isC[i]) coarse[i] = next++;
         HLevel nxt;
-        cur.P = direct_interpolation(cur.A, S, isC, coarse, (int32_t)nc);
+        cur.P = prm.interp == 1 ? extended_i_interpolation(cur.A, S, isC, coarse, (int32_t)nc, prm.p_max)
+                                : direct_interpolation(cur.A, S, isC, coarse, (int32_t)nc);
         cur.R = transpose(cur.P);
         nxt.A = galerkin_product(cur.R, cur.A, cur.P);
         cur.isC = std::move(isC);

@@ -414,3 +414,24 @@ def test_group_per_row_candidates_within_tolerance(case, precision):
     best, ms = capi.amgdd_autotune(s.h, 1, reps=2, allow_reordered=True)
     assert ms[18] > 0 and ms[19] > 0 and ms[best] <= 1.01 * ms[ms >= 0].min()
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["aniso2d", "poisson3d_24", "batch3"])
+def test_extended_i_hierarchy_solve_bit_exact(case, precision):
+    """With extended+i interpolation (truncated to 4 per row) the GPU solve
+    equals the oracle's on the same hierarchy bit for bit, FP64 and mixed."""
+    rp, ci, v, part, nsub, pad, b = _case(case)
+    o = Oracle(rp, ci, v, part, nsub, pad, interp="exti", pmax=4)
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, precision=precision, interp="exti", p_max=4)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x, tol=1e-8, max_iter=200)
+    xo, ho = o.amgdd_solve(b, 2, tol=1e-8, maxit=200, mixed=bool(precision))
+    assert info["converged"] and info["iterations"] == len(ho) - 1
+    assert np.array_equal(_host(x), xo)
+    assert np.allclose(info["history"], ho, rtol=1e-12, atol=0)
+    xv = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    iv = s.vcycle_solve(_dev(b), xv, tol=1e-8, max_iter=400)
+    xvo, hvo = o.vcycle_solve(b, tol=1e-8, maxit=400)
+    assert iv["iterations"] == len(hvo) - 1 and np.array_equal(_host(xv), xvo)
+    s.close()

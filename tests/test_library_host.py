@@ -162,3 +162,25 @@ def test_streamed_layout_uneven_batch():
     s = Solver(rp, ci, v, part, nsub, 2, host_only=3, precision=1, hybrid_level=1)
     assert s.stats.fac_fma > 0
     s.close()
+
+
+def test_fac_operation_count_only_extra_matvec():
+    """Algorithm 4's only mat-vec beyond a V-cycle's is the coarse-residual
+    recalculation f_{l+1} -= A_{l+1} u_{l+1}: skipped on the first downsweep
+    (u_{l+1} = 0) and never on the finest grid. The library's executed-fma
+    count over all composite grids must therefore be W1 + (n_fac - 1) W with
+    W - W1 = the stored entries of A_l's real rows on every level l >= 1."""
+    rp, ci, v = I.poisson3d(20, 20, 20)
+    part, nsub = I.box_partition((20, 20, 20), (10, 10, 5))
+    fma = {}
+    for nfac in (1, 2, 3):
+        s = Solver(rp, ci, v, part, nsub, 2, n_fac=nfac, host_only=2)
+        st = s.stats
+        fma[nfac] = st.fac_fma
+        extra = sum(st.comp_nnz_A[l] for l in range(1, st.num_levels))
+        s.close()
+    assert extra > 0
+    W1 = fma[1]
+    W = fma[2] - fma[1]
+    assert fma[3] - fma[2] == W
+    assert W - W1 == extra

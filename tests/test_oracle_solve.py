@@ -92,6 +92,14 @@ def test_full_mask_is_the_vcycle():
         for _ in range(nfac):
             xv = o.vcycle_apply(b, xv)
         assert abs(x1 - xv).max() <= 1e-14 * abs(xv).max()
+    # several subdomains whose padding covers the whole grid (eta >= the grid
+    # diameter on every level): every composite grid is the whole hierarchy,
+    # so the iteration equals the one-subdomain iteration bit for bit
+    part, nsub = I.box_partition((24, 20), (12, 10))
+    ow = Oracle(rp, ci, v, part, nsub, 50)
+    assert all(ow.comp_sizes(p, l)[0] == ow.level_n[l] for p in range(nsub) for l in range(ow.nlev))
+    for nfac in (1, 2):
+        assert np.array_equal(ow.amgdd_iteration(b, np.zeros(480), nfac), o.amgdd_iteration(b, np.zeros(480), nfac))
     # whole histories agree up to that rounding, which grows relative to the
     # shrinking residual (about 1e-15 * ||A|| ||x|| / ||r_k||)
     _, hd = o.amgdd_solve(b, 1, tol=1e-10)

@@ -184,3 +184,33 @@ def test_fac_operation_count_only_extra_matvec():
     W = fma[2] - fma[1]
     assert fma[3] - fma[2] == W
     assert W - W1 == extra
+
+
+def test_device_entry_points_refuse_host_only_handles():
+    """Every solve-phase entry point returns AMGDD_ERR_NOT_ON_DEVICE (9) on a
+    handle set up with host_only, and option values out of range are refused
+    at setup with AMGDD_ERR_INVALID_ARG (1); nothing needs a GPU."""
+    import ctypes as C
+    rp, ci, v = I.poisson2d(16, 16)
+    part, nsub = I.box_partition((16, 16), (8, 8))
+    s = Solver(rp, ci, v, part, nsub, 1, host_only=True)
+    lib = capi.load()
+    null = None
+    calls = [
+        lambda: lib.amgdd_fac(s.h, null, null, null),
+        lambda: lib.amgdd_fac_multi(s.h, null, null, 4, null),
+        lambda: lib.amgdd_iterate_multi(s.h, null, null, 4, null),
+        lambda: lib.amgdd_solve_multi(s.h, null, null, 4, 1e-8, 10, null, null),
+        lambda: lib.amgdd_set_fac_kernel(s.h, 1, 15),
+        lambda: lib.amgdd_autotune(s.h, 1, 1, 0, null, null, null),
+        lambda: lib.amg_vcycle(s.h, null, null, null),
+        lambda: lib.amg_hybrid_cycle(s.h, null, null, null),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == 9, k
+    assert lib.amgdd_autotune(None, 1, 1, 0, null, null, null) == 1
+    s.close()
+    for kw in ({"interp": 2}, {"p_max": -1}, {"precision": 2}, {"n_fac": 0}):
+        with pytest.raises(capi.AmgddError) as e:
+            Solver(rp, ci, v, part, nsub, 1, host_only=True, **kw)
+        assert e.value.status == 1, kw

@@ -111,3 +111,26 @@ def test_batched64_four_columns_sampled():
         rel = np.linalg.norm(Bh[:, j] - A @ Xh[:, j]) / np.linalg.norm(Bh[:, j])
         assert rel <= 1e-8 and np.isclose(rel, info["history"][j][-1], rtol=1e-6), j
     s.close()
+
+
+@pytest.mark.parametrize("interp", ["direct", "exti"])
+def test_aniso512_full_iteration_bit_exact(interp):
+    """The 512^2 rotated-anisotropy workload at full size (256 composite
+    grids): the oracle runs every grid here, so one AMG-DD iteration and one
+    V-cycle are compared on every unknown, with direct and extended+i
+    interpolation, in the autotuned launch configuration."""
+    w = I.workload("aniso2d_512", seed=0)
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], interp=interp)
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+               interp=interp)
+    capi.amgdd_autotune(s.h, 1, reps=1)
+    b = w["b"]
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    capi.amgdd_iterate(s.h, bd, x)
+    assert np.array_equal(x.cpu().numpy(), o.amgdd_iteration(b, np.zeros(s.n), w["n_fac"]))
+    x0 = np.random.default_rng(5).uniform(-1.0, 1.0, s.n)
+    xv = torch.from_numpy(x0.copy()).cuda()
+    capi.amg_vcycle(s.h, bd, xv)
+    assert np.array_equal(xv.cpu().numpy(), o.vcycle_apply(b, x0))
+    s.close()

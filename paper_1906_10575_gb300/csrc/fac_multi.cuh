@@ -212,10 +212,15 @@ __device__ __forceinline__ const T *stage(const Block &B, const T *__restrict__ 
     return x;
 }
 
+// One Jacobi half-sweep over rows [r0, r1): d = (f - V u) * (1/l1), then
+// u += d, t += d. in_place: no row of the pass reads u or t where another row
+// of the pass writes them (the F rows of the downsweep on l >= 1 read u at C
+// points only), so each row adds its own d at once: no scratch and no
+// barrier between the two steps, the same values.
 template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB>
 __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B, const FacLevelDesc &d, int g,
                                              const FacViewDev &V, int64_t s0, int first, int r0, int r1,
-                                             unsigned char *buf)
+                                             unsigned char *buf, bool in_place = false)
 {
     T *__restrict__ u = static_cast<T *>(P.u) + d.row0 * R;
     T *__restrict__ t = static_cast<T *>(P.t) + d.row0 * R;
@@ -223,6 +228,18 @@ __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B,
     const T *__restrict__ f = static_cast<const T *>(P.f) + d.row0 * R;
     const T *__restrict__ l1 = static_cast<const T *>(P.l1inv) + d.row0;
     const T *ux = stage<SB>(B, u, (int64_t)d.nBar * R, buf);
+    if (in_place) {
+        rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, ux, [&](int r, const VecR<T, R> &s) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const T v = (f[r * R + j] - s.v[j]) * l1[r];
+                u[r * R + j] = u[r * R + j] + v;
+                t[r * R + j] = t[r * R + j] + v;
+            }
+        });
+        __syncthreads();
+        return;
+    }
     rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, ux, [&](int r, const VecR<T, R> &s) {
 #pragma unroll
         for (int j = 0; j < R; ++j) dd[r * R + j] = (f[r * R + j] - s.v[j]) * l1[r];
@@ -315,7 +332,8 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                         }
                     }
                     __syncthreads();
-                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, fac_stage);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, fac_stage,
+                                                             true);
                 } else {
                     relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC, fac_stage);
                     relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal, fac_stage);

@@ -301,8 +301,10 @@ amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32
  *   k = 22..24: as 15, and every pass whose gathered level vector fits 16,
  *               32 or 44 KB copies it to shared memory first (16-bit local
  *               columns).
+ *   k = 25:     as 15, but blocks claim grids from one queue, largest first,
+ *               instead of from per-SM bins of estimated work.
  * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
-#define AMGDD_FAC_CANDIDATES 25
+#define AMGDD_FAC_CANDIDATES 26
 /* amgdd_autotune flags: also time candidates 18 and 19 (reordered row sums) */
 #define AMGDD_TUNE_ALLOW_REORDERED 1
 

@@ -86,6 +86,7 @@ struct amgdd_handle_s {
     // the group-per-row candidate uses (chosen from the level sizes at setup)
     int fac_cand[3] = {7, 9, 9};
     int8_t grp_level[kMaxLevels + 1] = {};
+    const int32_t *one_bin_off = nullptr;   // {0, nsub}: every grid in one bin (global queue)
     int hyb_level = -1;
     FacParams fac_hyb{};
     double *r_hyb = nullptr;
@@ -395,6 +396,12 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, FacStream &S, int nl
     // the 16 warps of a block and 2g entries still fit the mean real row
     if (&P == &h->fac) {
         h->fac_cand[0] = P.schedule - 1;   // the options' schedule until changed
+        {
+            std::vector<int32_t> ob{0, nsub};
+            int32_t *dob;
+            UP(ob, &dob, "upload queue bounds");
+            h->one_bin_off = dob;
+        }
         for (int l = 0; l < nlev && l <= kMaxLevels; ++l) {
             double slices = 0.0, rows = 0.0;
             for (int p = 0; p < nsub; ++p) {
@@ -924,6 +931,12 @@ static cudaError_t launch_candidate(amgdd_handle h, FacParams P, int nrhs, int k
         return launch_fac_all_grids(P, P.nsub, h->threads, st);
     }
     if (k < 18) return launch_fac_multi(P, P.nsub, nrhs, k - 8, st);
+    if (k == 25) {   // variant 7 claiming from one queue, largest grid first
+        P.nbins = 1;
+        P.bin_off = h->one_bin_off;
+        P.bin_grid = P.order;
+        return launch_fac_multi(P, P.nsub, nrhs, 7, st);
+    }
     if (k >= 20) return launch_fac_multi(P, P.nsub, nrhs, k - 9, st);   // variants 11-15
     for (int l = 0; l <= kMaxLevels; ++l) P.grp[l] = k == 18 ? h->grp_level[l] : (int8_t)32;
     return launch_fac_multi(P, P.nsub, nrhs, 10, st);
@@ -1400,7 +1413,9 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
 // grids have schedules 1 and 8), 9 <= k < 18 the several-column kernel's
 // variant k - 8, 18 and 19 its group-per-row variant (lanes per row by level
 // size, or 32 on every level), whose row sums are not the ascending chain,
-// 20-24 its variants 11-15 (L1 prefetch, shared-memory staging).
+// 20-24 its variants 11-15 (L1 prefetch, shared-memory staging), 25 its
+// variant 7 with every grid in one queue (largest first) instead of per-SM
+// bins.
 static bool candidate_applies(amgdd_handle h, int nrhs, int k)
 {
     if (k < 0 || k >= AMGDD_FAC_CANDIDATES) return false;

@@ -472,10 +472,13 @@ cudaError_t launch_fac_r_variant(const FacParams &P, int nsub, cudaStream_t st)
 {
     static_assert(SB % 16 == 0 && SB <= 44 * 1024, "staging buffer plus static shared memory within 48 KB");
     auto kern = dev::k_fac_all_grids_r<CI, T, R, UNR, MINB, PF, GRP, SB>;
-    int per_sm = 0;
+    int per_sm = 0, dev = 0, nsm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, SB);
     if (e != cudaSuccess) return e;
-    int ctas = (per_sm < 1 ? 1 : per_sm) * P.nbins;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    // every block that fits at once (the bins only say where blocks look first)
+    int ctas = (per_sm < 1 ? 1 : per_sm) * (nsm < 1 ? 1 : nsm);
     if (ctas > nsub) ctas = nsub;
     if ((e = cudaMemsetAsync(P.ctr, 0, sizeof(int32_t) * (size_t)P.nbins, st)) != cudaSuccess) return e;
     kern<<<ctas, 512, SB, st>>>(P);

@@ -298,11 +298,17 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
             for (int r = B.tid; r < d.nBar; r += B.nt) {
                 const int64_t i = d.row0 + r;
                 const int64_t g = P.gmap[i];
+                // t accumulates from zero on every level; u_0 and s_0 start at
+                // zero and nothing else writes s_0; u_l and s_l (l >= 1) are
+                // written before they are read (the downsweep initialises u_l,
+                // the restriction from level l-1 writes s_l)
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    Pu[i * R + j] = T(0);
                     Pt[i * R + j] = T(0);
-                    Ps[i * R + j] = T(0);
+                    if (l == 0) {
+                        Pu[i * R + j] = T(0);
+                        Ps[i * R + j] = T(0);
+                    }
                     if (r < d.nReal) Pf[i * R + j] = (T)rl[g * R + j];
                 }
             }
@@ -396,11 +402,9 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
                             });
                     }
                     T *__restrict__ t = Pt + d.row0 * R;
-                    T *__restrict__ s = Ps + d.row0 * R;
-                    for (int r = B.tid; r < d.nBar * R; r += B.nt) {
-                        t[r] = T(0);
-                        s[r] = T(0);
-                    }
+                    // reset t_l; s_l needs no reset (s_0 stays zero, the next
+                    // downsweep's restriction overwrites s_l for l >= 1)
+                    for (int r = B.tid; r < d.nBar * R; r += B.nt) t[r] = T(0);
                 }
                 __syncthreads();
             }

@@ -90,8 +90,10 @@ cudaError_t launch_relax_apply(const int32_t *rowid, int64_t r0, int64_t r1, con
 cudaError_t launch_coarse_solve(const double *ainv, int n, const double *f, double *u, cudaStream_t st);
 cudaError_t launch_fac_all_grids(const FacParams &P, int nsub, int threads, cudaStream_t st);
 // several right-hand sides (nrhs = 2 or 4), vectors stored row by row
-// Composite-grid kernel for nrhs = 1, 2 or 4 columns, variant 1..6 (see
-// fac_multi.cuh); the per-column launchers live in fac_multi_r*.cu.
+// Composite-grid kernel for nrhs = 1, 2 or 4 columns, variant 1..15 (see
+// fac_multi.cuh; every variant but the group-per-row variant 10 keeps each
+// row's ascending fma chain, and 10 reorders row sums the same way for every
+// column); the per-column launchers live in fac_multi_r*.cu.
 cudaError_t launch_fac_multi(const FacParams &P, int nsub, int nrhs, int variant, cudaStream_t st);
 cudaError_t launch_fac_multi_1(const FacParams &P, int nsub, int variant, cudaStream_t st);
 cudaError_t launch_fac_multi_2(const FacParams &P, int nsub, int variant, cudaStream_t st);

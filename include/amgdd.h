@@ -342,10 +342,11 @@ amgdd_status amgdd_kappa_grad_3d(int32_t nx, int32_t ny, int32_t nz, const doubl
 
 /* ---- residual without any device allocation ------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
- * cannot call cudaMalloc at the moment they need a residual, for example code
- * recording a CUDA graph (allocation is not a stream-ordered call and must not
- * run during capture) or a process whose device memory belongs to its own pool
- * allocator. It needs no setup handle and allocates nothing: the matrix and
+ * cannot call cudaMalloc at the moment they need a residual, for example a
+ * process whose device memory was handed to its own pool allocator at start-up
+ * (a raw allocation then fails or breaks its memory budget), or a latency-bound
+ * loop that cannot pay for cudaMalloc/cudaFree (which can take milliseconds;
+ * cudaFree waits for the device). It needs no setup handle and allocates nothing: the matrix and
  * vectors are the caller's, and the per-block partial sums of the norm live in
  * a 32 KiB file-scope device array that every GPU loading the library holds
  * until the process exits.

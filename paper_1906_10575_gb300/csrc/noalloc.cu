@@ -3,12 +3,13 @@
 // file-scope device array instead of memory the library would allocate.
 //
 // Who needs this: code that cannot call cudaMalloc when it wants a residual.
-// Typical cases are a caller in the middle of CUDA stream capture (cudaMalloc
-// is not a stream-ordered call and must not run while a graph is recorded),
-// and a framework or serving process whose device memory is owned by its own
-// pool allocator or budget, where stray raw allocations are forbidden. Such a
-// caller keeps the matrix and vectors in memory it already owns and gets the
-// residual without a setup handle.
+// A framework or serving process often hands all device memory to its own
+// pool allocator at start-up and accounts for every byte, so a raw cudaMalloc
+// from a library either fails (the pool already holds the memory) or breaks
+// its budget; and a latency-bound loop cannot afford cudaMalloc/cudaFree
+// inside it (both can take milliseconds, and cudaFree waits for the device).
+// Such a caller keeps the matrix and vectors in memory it already owns and
+// gets the residual without a setup handle.
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -1,9 +1,10 @@
 """The allocation-free residual entry point against the handle-based one.
 
 amgdd_residual_csr_noalloc exists for callers that cannot call cudaMalloc when
-they need a residual (code recording a CUDA graph, processes whose device
-memory belongs to their own pool allocator): it takes a device CSR the caller
-owns and keeps its reduction scratch in a static device array. Two calls in a
+they need a residual (processes whose device memory was handed to their own
+pool allocator, where a raw allocation fails or breaks the budget; loops that
+cannot pay for an allocation's latency): it takes a device CSR the caller owns
+and keeps its reduction scratch in a static device array. Two calls in a
 row must each match amgdd_residual of a set-up handle: r bit for bit (same
 ascending fma chain per row), the squared norm to 1e-12 relative (the block
 partition of the reduction differs).

@@ -303,8 +303,16 @@ amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32
  *               columns).
  *   k = 25:     as 15, but blocks claim grids from one queue, largest first,
  *               instead of from per-SM bins of estimated work.
+ *   k = 26, 27: one queue as 25, no prefetch, and each grid's six work
+ *               vectors held in the block's shared memory from its prologue
+ *               to its epilogue, operators loaded cacheable in L1 (for small
+ *               grids, whose phases are bound by the latency of reading what
+ *               the previous phase wrote): 26: 2 entries in flight, 2 blocks
+ *               per SM; 27: 4 entries, 1 block. The shared memory is sized
+ *               for the largest grid; when that exceeds the per-block limit,
+ *               the vectors stay in global memory (16-bit local columns).
  * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
-#define AMGDD_FAC_CANDIDATES 26
+#define AMGDD_FAC_CANDIDATES 28
 /* amgdd_autotune flags: also time candidates 18 and 19 (reordered row sums) */
 #define AMGDD_TUNE_ALLOW_REORDERED 1
 

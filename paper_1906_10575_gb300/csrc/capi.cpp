@@ -466,6 +466,12 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, FacStream &S, int nl
         P.bin_grid = dgrid;
         P.ctr = dctr;
     }
+    P.max_grid_rows = 0;
+    for (int p = 0; p < nsub; ++p) {
+        const FacLevelDesc &a = F.desc[(size_t)p * nlev], &z = F.desc[(size_t)p * nlev + nlev - 1];
+        P.max_grid_rows = std::max<int64_t>(P.max_grid_rows, z.row0 + z.nBar - a.row0);
+    }
+    P.vsm_bytes = 0;
     P.desc = dd;
     P.order = ord;
     P.gmap = static_cast<const int32_t *>(gm);
@@ -931,11 +937,11 @@ static cudaError_t launch_candidate(amgdd_handle h, FacParams P, int nrhs, int k
         return launch_fac_all_grids(P, P.nsub, h->threads, st);
     }
     if (k < 18) return launch_fac_multi(P, P.nsub, nrhs, k - 8, st);
-    if (k == 25) {   // variant 7 claiming from one queue, largest grid first
+    if (k == 25 || k == 26 || k == 27) {   // one queue, largest grid first
         P.nbins = 1;
         P.bin_off = h->one_bin_off;
         P.bin_grid = P.order;
-        return launch_fac_multi(P, P.nsub, nrhs, 7, st);
+        return k == 25 ? launch_fac_multi(P, P.nsub, nrhs, 7, st) : launch_fac_vsm(P, P.nsub, nrhs, k - 25, st);
     }
     if (k >= 20) return launch_fac_multi(P, P.nsub, nrhs, k - 9, st);   // variants 11-15
     for (int l = 0; l <= kMaxLevels; ++l) P.grp[l] = k == 18 ? h->grp_level[l] : (int8_t)32;
@@ -1415,7 +1421,9 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
 // size, or 32 on every level), whose row sums are not the ascending chain,
 // 20-24 its variants 11-15 (L1 prefetch, shared-memory staging), 25 its
 // variant 7 with every grid in one queue (largest first) instead of per-SM
-// bins.
+// bins, 26 and 27 the kernel that keeps each grid's work vectors in shared
+// memory (two entries in flight and two blocks per SM, or four and one) on
+// that queue.
 static bool candidate_applies(amgdd_handle h, int nrhs, int k)
 {
     if (k < 0 || k >= AMGDD_FAC_CANDIDATES) return false;

@@ -76,6 +76,11 @@ struct FacParams {
     // lanes per row on each level in the group-per-row kernel variant
     // (powers of two up to 32; 1 = one row per lane)
     int8_t grp[kMaxLevels + 1];
+    // rows of the largest composite grid (all its levels), and the dynamic
+    // shared memory per block that holds a grid's work vectors in the
+    // variants that keep them on chip (0: none; set by their launcher)
+    int64_t max_grid_rows;
+    int64_t vsm_bytes;
 };
 
 cudaError_t launch_residual(const SellView &A, const double *b, const double *x, double *r, double *partial,
@@ -98,6 +103,11 @@ cudaError_t launch_fac_multi(const FacParams &P, int nsub, int nrhs, int variant
 cudaError_t launch_fac_multi_1(const FacParams &P, int nsub, int variant, cudaStream_t st);
 cudaError_t launch_fac_multi_2(const FacParams &P, int nsub, int variant, cudaStream_t st);
 cudaError_t launch_fac_multi_4(const FacParams &P, int nsub, int variant, cudaStream_t st);
+// Composite-grid kernel with each grid's work vectors in shared memory
+// (fac_vsm.cu) for nrhs = 1, 2 or 4 columns: variant 1 = two operator entries
+// in flight, two blocks per SM; 2 = four entries, one block. Needs 16-bit
+// local columns.
+cudaError_t launch_fac_vsm(const FacParams &P, int nsub, int nrhs, int variant, cudaStream_t st);
 cudaError_t launch_residual_multi(const SellView &A, const double *b, const double *x, double *r, double *partial,
                                   int nblocks, double *out, int nrhs, cudaStream_t st);
 cudaError_t launch_sumsq_multi(const double *v, int64_t n, double *partial, int nblocks, double *out, int nrhs,

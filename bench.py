@@ -304,7 +304,8 @@ def run_extra(args, name, stream, dist, local):
     import torch
     from paper_1906_10575_gb300 import Solver, capi
 
-    w = I.workload(name, seed=0, nsys=args.nsys if "nsys" in I.WORKLOADS[name] else None)
+    shape = (args.edge, args.edge) if name == "poisson2d_64" and args.edge > 0 else None
+    w = I.workload(name, seed=0, nsys=args.nsys if "nsys" in I.WORKLOADS[name] else None, shape=shape)
     n = int(len(w["rowptr"]) - 1)
     hbm, peak_kind = _peaks()
     multi = "nsys" in I.WORKLOADS[name]
@@ -417,8 +418,8 @@ def run_extra(args, name, stream, dist, local):
                 "FP32 AlgFAC / FP64 refinement" % (len(w["edges"]), ",".join(map(str, sorted(set(w["edges"])))),
                                                      n, w["nsub"], nrhs))
     elif small:
-        desc = ("2D 5-point Poisson 64^2 (N=%d), %d subdomains of 16^2, padding 1, 2 AlgFAC V(1,1) per "
-                "iteration, FP64, b~U[-1,1] seed 0, x0=0" % (n, w["nsub"]))
+        desc = ("2D 5-point Poisson %d^2 (N=%d), %d subdomains of 16^2, padding 1, 2 AlgFAC V(1,1) per "
+                "iteration, FP64, b~U[-1,1] seed 0, x0=0" % (w["shape"][0], n, w["nsub"]))
     elif "aniso" in I.WORKLOADS[name]:
         desc = ("2D rotated anisotropic diffusion theta=3pi/16, eps=1e-3, 9-point, 512^2 (N=%d), %d subdomains "
                 "of 32^2, padding 2, FP64, b~U[-1,1] seed 0" % (n, w["nsub"]))
@@ -560,6 +561,9 @@ def main():
                          "truncated to 4 entries per row")
     ap.add_argument("--candidate", type=int, default=-1,
                     help="use this FAC kernel candidate instead of autotuning (profiling captures)")
+    ap.add_argument("--edge", type=int, default=0,
+                    help="poisson2d_64: grid edge (default 64, the workload; other edges size the "
+                         "latency-bound regime)")
     ap.add_argument("--nsys", type=int, default=64,
                     help="batched_64: number of systems (default 64, the workload; fewer are for "
                          "profiling captures only)")

@@ -51,16 +51,19 @@ def _config(w):
 
 
 # FAC kernel of each autotuner candidate: the single-column kernel (schedules
-# 1-9, source kernels.cu), the several-column kernel (source fac_multi.cuh) or
-# the one with each grid's work vectors in shared memory (fac_vsm.cu)
+# 1-9, source kernels.cu), the several-column kernel (source fac_multi.cuh),
+# the one with each grid's work vectors in shared memory (fac_vsm.cu) or the
+# one cycling each grid with a cluster of blocks (fac_cluster.cu)
 FAC_KERNELS = {"k_fac_all_grids": "kernels.cu", "k_fac_all_grids_r": "fac_multi.cuh",
-               "k_fac_grids_vsm": "fac_vsm.cu"}
+               "k_fac_grids_vsm": "fac_vsm.cu", "k_fac_cluster": "fac_cluster.cu"}
 
 
 def _fac_kernel(candidate):
     if candidate is None or candidate < 9:
         return "k_fac_all_grids"
-    return "k_fac_grids_vsm" if candidate in (26, 27) else "k_fac_all_grids_r"
+    if candidate in (26, 27):
+        return "k_fac_grids_vsm"
+    return "k_fac_cluster" if candidate >= 28 else "k_fac_all_grids_r"
 
 
 def _measured_traffic(n_edge, kernel, candidate):

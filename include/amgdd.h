@@ -311,8 +311,12 @@ amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32
  *               per SM; 27: 4 entries, 1 block. The shared memory is sized
  *               for the largest grid; when that exceeds the per-block limit,
  *               the vectors stay in global memory (16-bit local columns).
+ *   k = 28..30: one queue as 25, each grid cycled by a thread-block cluster
+ *               of 2, 4 or 8 blocks of 512 threads instead of one block, the
+ *               phases separated by cluster barriers (for launches over fewer
+ *               grids than SMs; 16-bit local columns).
  * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
-#define AMGDD_FAC_CANDIDATES 28
+#define AMGDD_FAC_CANDIDATES 31
 /* amgdd_autotune flags: also time candidates 18 and 19 (reordered row sums) */
 #define AMGDD_TUNE_ALLOW_REORDERED 1
 

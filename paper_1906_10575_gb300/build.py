@@ -20,7 +20,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 
 CU_SOURCES = ["kernels.cu", "kernels_multi.cu", "fac_multi_r1.cu", "fac_multi_r2.cu", "fac_multi_r4.cu",
-              "fac_vsm.cu", "adjoint.cu", "noalloc.cu"]
+              "fac_vsm.cu", "fac_cluster.cu", "adjoint.cu", "noalloc.cu"]
 CXX_SOURCES = ["hierarchy.cpp", "composite.cpp", "capi.cpp"]
 
 

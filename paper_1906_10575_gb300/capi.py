@@ -67,7 +67,7 @@ EXPORTS = [
     "amgdd_set_fac_kernel", "amgdd_autotune",
 ]
 
-FAC_CANDIDATES = 28
+FAC_CANDIDATES = 31
 TUNE_ALLOW_REORDERED = 1
 
 _lib = None

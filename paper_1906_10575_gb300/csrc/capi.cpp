@@ -937,11 +937,13 @@ static cudaError_t launch_candidate(amgdd_handle h, FacParams P, int nrhs, int k
         return launch_fac_all_grids(P, P.nsub, h->threads, st);
     }
     if (k < 18) return launch_fac_multi(P, P.nsub, nrhs, k - 8, st);
-    if (k == 25 || k == 26 || k == 27) {   // one queue, largest grid first
+    if (k >= 25) {   // one queue, largest grid first
         P.nbins = 1;
         P.bin_off = h->one_bin_off;
         P.bin_grid = P.order;
-        return k == 25 ? launch_fac_multi(P, P.nsub, nrhs, 7, st) : launch_fac_vsm(P, P.nsub, nrhs, k - 25, st);
+        if (k == 25) return launch_fac_multi(P, P.nsub, nrhs, 7, st);
+        if (k <= 27) return launch_fac_vsm(P, P.nsub, nrhs, k - 25, st);
+        return launch_fac_cluster(P, P.nsub, nrhs, 1 << (k - 27), st);   // clusters of 2, 4, 8 blocks
     }
     if (k >= 20) return launch_fac_multi(P, P.nsub, nrhs, k - 9, st);   // variants 11-15
     for (int l = 0; l <= kMaxLevels; ++l) P.grp[l] = k == 18 ? h->grp_level[l] : (int8_t)32;
@@ -1423,7 +1425,8 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
 // variant 7 with every grid in one queue (largest first) instead of per-SM
 // bins, 26 and 27 the kernel that keeps each grid's work vectors in shared
 // memory (two entries in flight and two blocks per SM, or four and one) on
-// that queue.
+// that queue, 28-30 the kernel that cycles each grid with a cluster of 2, 4
+// or 8 blocks, on that queue.
 static bool candidate_applies(amgdd_handle h, int nrhs, int k)
 {
     if (k < 0 || k >= AMGDD_FAC_CANDIDATES) return false;
@@ -1501,7 +1504,17 @@ amgdd_status amgdd_autotune(amgdd_handle h, int32_t nrhs, int32_t reps, int32_t 
         if (!candidate_applies(h, nrhs, k)) continue;
         if (candidate_reorders(k) && !(flags & AMGDD_TUNE_ALLOW_REORDERED)) continue;
         auto launch = [&]() -> cudaError_t { return launch_candidate(h, P, nrhs, k, st); };
-        if ((e = launch()) != cudaSuccess) break;           // warm-up
+        if ((e = launch()) != cudaSuccess) {                // warm-up
+            // a cluster shape this device cannot schedule is refused before
+            // anything runs: that candidate does not apply here
+            if (k >= 28 && (e == cudaErrorInvalidConfiguration || e == cudaErrorInvalidClusterSize ||
+                            e == cudaErrorLaunchOutOfResources)) {
+                cudaGetLastError();
+                e = cudaSuccess;
+                continue;
+            }
+            break;
+        }
         if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
         if (e != cudaSuccess) break;

@@ -108,6 +108,10 @@ cudaError_t launch_fac_multi_4(const FacParams &P, int nsub, int variant, cudaSt
 // in flight, two blocks per SM; 2 = four entries, one block. Needs 16-bit
 // local columns.
 cudaError_t launch_fac_vsm(const FacParams &P, int nsub, int nrhs, int variant, cudaStream_t st);
+// Composite-grid kernel cycling each grid with a cluster of K = 1..8 blocks
+// (fac_cluster.cu), grids claimed from one queue (P.nbins == 1), for nrhs =
+// 1, 2 or 4 columns. Needs 16-bit local columns.
+cudaError_t launch_fac_cluster(const FacParams &P, int nsub, int nrhs, int K, cudaStream_t st);
 cudaError_t launch_residual_multi(const SellView &A, const double *b, const double *x, double *r, double *partial,
                                   int nblocks, double *out, int nrhs, cudaStream_t st);
 cudaError_t launch_sumsq_multi(const double *v, int64_t n, double *partial, int nblocks, double *out, int nrhs,

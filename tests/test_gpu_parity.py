@@ -333,7 +333,7 @@ def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
     ref = [step(Bh[:, j], np.zeros(n), 2) for j in range(4)]
     b = _dev(Bh[:, 0])
     single = [0, 7] if precision else list(range(9))
-    exact = single + list(range(9, 18)) + list(range(20, 28))    # 18, 19 reorder row sums: tested below
+    exact = single + list(range(9, 18)) + list(range(20, 31))    # 18, 19 reorder row sums: tested below
     for k in exact:
         capi.amgdd_set_fac_kernel(s.h, 1, k)
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -341,14 +341,14 @@ def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
         assert np.array_equal(_host(x), ref[0]), k
     for nrhs in (2, 4):
         B = torch.from_numpy(np.ascontiguousarray(Bh[:, :nrhs])).cuda()
-        for k in list(range(9, 18)) + list(range(20, 28)):
+        for k in list(range(9, 18)) + list(range(20, 31)):
             capi.amgdd_set_fac_kernel(s.h, nrhs, k)
             X = torch.zeros((n, nrhs), dtype=torch.float64, device="cuda")
             capi.amgdd_iterate_multi(s.h, B, X)
             Xh = _host(X)
             for j in range(nrhs):
                 assert np.array_equal(Xh[:, j], ref[j]), (nrhs, k, j)
-    for k in ([1, 2, 3, 4, 5, 6, 8] if precision else []) + [28, -1]:
+    for k in ([1, 2, 3, 4, 5, 6, 8] if precision else []) + [31, -1]:
         with pytest.raises(capi.AmgddError):
             capi.amgdd_set_fac_kernel(s.h, 1, k)
     with pytest.raises(capi.AmgddError):

@@ -320,10 +320,14 @@ def test_hybrid_amgdd_bit_exact(case):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", ["poisson3d_24", "kappa3d", "batch3", "poisson2d_64"])
 def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
-    """Every FAC kernel the autotuner may choose (the single-column schedules
-    and the several-column kernel's variants, for 1, 2 and 4 columns) gives
-    the oracle's iterate bit for bit; the autotuner keeps one of them and the
-    solve after it is unchanged."""
+    """Every FAC kernel the autotuner may choose (the single-column schedules,
+    the several-column kernel's variants, the kernel holding each grid's work
+    vectors in shared memory and the one cycling each grid with a cluster of
+    blocks, for 1, 2 and 4 columns) gives the oracle's iterate bit for bit;
+    the autotuner keeps one of them and the solve after it is unchanged. On
+    the 64^2 case every grid's vectors fit shared memory at every width and
+    precision; the 3D cases take both paths of that kernel (on chip for one
+    FP32 column, in global memory at four columns)."""
     rp, ci, v, part, nsub, pad, _ = _case(case)
     o = Oracle(rp, ci, v, part, nsub, pad)
     s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, precision=precision)

@@ -159,7 +159,10 @@ amgdd_status amgdd_box_partition(int32_t nx, int32_t ny, int32_t nz, int32_t bx,
  *   stream  : stream for the upload (ignored when opts->host_only).
  *   out     : receives the handle (NULL on failure).
  * Errors: INVALID_ARG, NOT_SYMMETRIC, SINGULAR, HIERARCHY_ASSUMPTION (only with
- * opts->strict_assumption), OOM, CUDA. */
+ * opts->strict_assumption), OOM, CUDA. A failed setup frees everything it had
+ * allocated. Testing of those paths: with AMGDD_FAULT_ALLOC=k (k >= 1) in the
+ * environment, the k-th device or pinned host allocation of this call fails
+ * as if memory were exhausted (OOM), without allocating. */
 amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub,
                          const int32_t *padding, int32_t npadding, const amgdd_options *opts,
                          void *stream, amgdd_handle *out);

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -114,13 +115,50 @@ amgdd_status cuda_fail(amgdd_handle h, cudaError_t e, const char *what)
         if (_e != cudaSuccess) return cuda_fail(h, _e, what);           \
     } while (0)
 
+// Allocation fault injection (for tests of the failure paths): while
+// amgdd_setup runs with AMGDD_FAULT_ALLOC=k (k >= 1) in the environment, its
+// k-th device or pinned host allocation fails as if memory were exhausted,
+// without allocating. Counted per calling thread; off outside amgdd_setup.
+thread_local int64_t t_fault_at = 0;
+thread_local int64_t t_alloc_seq = 0;
+
+bool inject_alloc_fault()
+{
+    return t_fault_at > 0 && ++t_alloc_seq == t_fault_at;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_malloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(p, bytes);
+}
+
+// Arms the injection for one amgdd_setup call and disarms it on every return.
+struct FaultScope {
+    FaultScope()
+    {
+        const char *v = std::getenv("AMGDD_FAULT_ALLOC");
+        t_fault_at = v ? std::atoll(v) : 0;
+        t_alloc_seq = 0;
+    }
+    ~FaultScope() { t_fault_at = 0; }
+};
+
 template <class T>
 cudaError_t upload(amgdd_handle h, const std::vector<T> &v, T **out, cudaStream_t st)
 {
     *out = nullptr;
     const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = dev_malloc(&p, bytes);
     if (e != cudaSuccess) return e;
     h->allocs.push_back(p);
     h->dev_bytes += (int64_t)bytes;
@@ -138,7 +176,7 @@ cudaError_t alloc(amgdd_handle h, size_t count, T **out)
     *out = nullptr;
     void *p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = dev_malloc(&p, bytes);
     if (e != cudaSuccess) return e;
     h->allocs.push_back(p);
     h->dev_bytes += (int64_t)bytes;
@@ -273,7 +311,7 @@ struct FacStream {
         if (g.n + bytes > g.cap) {
             const size_t nc = std::max({g.cap * 2, g.n + bytes, (size_t)1 << 20});
             void *p = nullptr;
-            if ((e = cudaMalloc(&p, nc)) != cudaSuccess) return e;
+            if ((e = dev_malloc(&p, nc)) != cudaSuccess) return e;
             if (g.n && (e = cudaMemcpyAsync(p, g.d, g.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) {
                 cudaFree(p);
                 return e;
@@ -346,7 +384,7 @@ cudaError_t settle(amgdd_handle h, DevGrow &g, cudaStream_t st, void **out)
     *out = nullptr;
     void *p = nullptr;
     const size_t bytes = std::max<size_t>(g.n, 16);
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = dev_malloc(&p, bytes);
     if (e != cudaSuccess) return e;
     h->allocs.push_back(p);
     h->dev_bytes += (int64_t)bytes;
@@ -570,6 +608,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
 {
     if (!out) return fail(nullptr, AMGDD_ERR_INVALID_ARG, "null output handle pointer");
     *out = nullptr;
+    const FaultScope fault_scope;
     const auto t0 = std::chrono::steady_clock::now();
     amgdd_status st;
     std::string why = validate(A, part, nsub, padding, npadding, st);
@@ -732,6 +771,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
                 amgdd_status s2 = cuda_fail(nullptr, e, what);
                 for (void *p : h->allocs) cudaFree(p);
                 h->allocs.clear();
+                if (h->h_scal) cudaFreeHost(h->h_scal);
                 delete h;
                 return s2;
             };
@@ -792,7 +832,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
             h->nred = 152 * 8;
             if ((e = alloc(h, (size_t)h->nred, &h->partial)) != cudaSuccess) return bail(e, "alloc partial");
             if ((e = alloc(h, 8, &h->scal)) != cudaSuccess) return bail(e, "alloc scalars");
-            if ((e = cudaMallocHost((void **)&h->h_scal, 8 * sizeof(double))) != cudaSuccess)
+            if ((e = pinned_malloc((void **)&h->h_scal, 8 * sizeof(double))) != cudaSuccess)
                 return bail(e, "alloc pinned");
             // composite-grid layout
             {
@@ -820,6 +860,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
         h->stats.device_bytes = h->dev_bytes;
     } catch (const std::bad_alloc &) {
         for (void *p : h->allocs) cudaFree(p);
+        if (h->h_scal) cudaFreeHost(h->h_scal);
         delete h;
         return fail(nullptr, AMGDD_ERR_OOM, "host allocation failed during setup");
     }

@@ -195,3 +195,28 @@ def test_hybrid_limits_and_convergence():
         x, h = o.hybrid_solve(lev0, b, 2, tol=1e-12)
         assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
         assert np.all(np.diff(h) < 0)
+
+
+@pytest.mark.parametrize("modes", [[(1, 1)], [(3, 2), (17, 11)]])
+def test_dirichlet_eigenvector_right_hand_side_gives_v_over_lambda(modes):
+    """b = sum of Dirichlet Laplacian eigenvectors v_ab (closed form, not a
+    factorisation): both solvers must return sum v_ab / lambda_ab. The
+    relative error is at most the relative residual times the condition
+    number (209 on this grid): 2.1e-11 for a 1e-13 residual; the test allows
+    2e-10."""
+    nx, ny = 24, 20
+    o, A, _ = _problem2d(nx, ny, (8, 10), 1)
+    i = np.arange(1, nx + 1)[:, None]
+    j = np.arange(1, ny + 1)[None, :]
+    b = np.zeros(nx * ny)
+    xe = np.zeros(nx * ny)
+    for a, c in modes:
+        # lexicographic numbering, i fastest: entry (i, j) is at i - 1 + nx (j - 1)
+        v = (np.sin(a * np.pi * i / (nx + 1)) * np.sin(c * np.pi * j / (ny + 1))).T.ravel()
+        lam = 4 - 2 * np.cos(a * np.pi / (nx + 1)) - 2 * np.cos(c * np.pi / (ny + 1))
+        b += v
+        xe += v / lam
+    assert np.allclose(A @ xe, b, rtol=0, atol=1e-12)
+    for x, h in (o.amgdd_solve(b, 2, tol=1e-13, maxit=400), o.vcycle_solve(b, tol=1e-13, maxit=800)):
+        assert h[-1] <= 1e-13
+        assert np.linalg.norm(x - xe) <= 2e-10 * np.linalg.norm(xe)

@@ -98,7 +98,16 @@ typedef struct {
     int32_t p_max;          /* extended+i only: keep the p_max largest |weights|
                                per row, rescaled to the row's sum (0 = keep
                                all; default 4) */
-    int32_t reserved[3];
+    int32_t coarsen;        /* C/F splitting (Section 2; the paper uses the HMIS
+                               of the hypre defaults without restating it):
+                               0 = Ruge-Stueben first pass (default); 1 = HMIS
+                               with the subdomains as the processors: the first
+                               pass on each subdomain's own strong connections,
+                               its C points at subdomain-interior points seeding
+                               PMIS on the whole strength graph, whose random
+                               tie-break is SplitMix64 of (level << 40) + point
+                               index (reproducible) */
+    int32_t reserved[2];
 } amgdd_options;
 
 /* Statistics of a completed setup. */

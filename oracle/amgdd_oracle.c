@@ -27,7 +27,9 @@
  *   - coarsening: Ruge-Stueben first pass, measure
  *     lambda_i = |S_i^T n U| + 2 |S_i^T n F|, largest measure first, ties to
  *     the smallest index; points with no strong connection in either
- *     direction become F points with an empty interpolation row;
+ *     direction become F points with an empty interpolation row; or
+ *     (coarsen = 1) HMIS with the subdomains as processors and a SplitMix64
+ *     draw in place of PMIS's random numbers (hmis_coarsen below);
  *   - interpolation: direct interpolation over strong C neighbours with
  *     positive off-diagonals lumped into the diagonal; or (interp = 1) the
  *     extended+i interpolation of the hypre defaults the paper names, with
@@ -216,6 +218,111 @@ static int *rs_coarsen(int n, const int64_t *srp, const int *sci)
     }
     free(h.a);
     free(lam);
+    free(trp);
+    free(tci);
+    return state;
+}
+
+/* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the output for counter x. It stands in for the
+ * random part of the PMIS measure below, so that the coarsening is
+ * reproducible: point i of level l draws splitmix64((l << 40) + i). */
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* PMIS order of two points: i before j when |S_i^T| is larger, then when
+ * its SplitMix64 draw is larger, then when its index is smaller. */
+static int pmis_before(int i, int j, const int64_t *trp, const uint64_t *draw)
+{
+    int64_t ci = trp[i + 1] - trp[i], cj = trp[j + 1] - trp[j];
+    if (ci != cj) return ci > cj;
+    if (draw[i] != draw[j]) return draw[i] > draw[j];
+    return i < j;
+}
+
+/* HMIS coarsening (the coarsening of the hypre defaults that Section 6 names;
+ * the paper does not restate it, this follows the published definition of De
+ * Sterck, Yang and Heys, SIAM J. Matrix Anal. Appl. 27 (2006)), with the
+ * subdomains in the role of the processors (sub[i] = subdomain of point i):
+ *  1. the Ruge-Stueben first pass (rs_coarsen) on each subdomain alone, i.e.
+ *     on the strong connections between points of the same subdomain;
+ *  2. its C points that are interior (no strong connection, in either
+ *     direction, to a point of another subdomain) are the first independent
+ *     set of PMIS on the whole strength graph: they are C, everything else
+ *     undecided;
+ *  3. PMIS: undecided points on which no point depends strongly (|S_i^T| = 0)
+ *     become F; then repeat: every undecided point that strongly depends on a
+ *     C point becomes F; stop when none is undecided; else every undecided
+ *     point that comes before all its undecided strong neighbours (S_i and
+ *     S_i^T, in the order of pmis_before) becomes C.
+ * With one subdomain every point is interior and the result is the first
+ * pass itself. Returns 1 (C) / 2 (F) per point, like rs_coarsen. */
+static int *hmis_coarsen(int n, const int64_t *srp, const int *sci, const int *sub, int level)
+{
+    /* 1. first pass on the same-subdomain connections */
+    int64_t *lrp = xmalloc(sizeof(int64_t) * ((size_t)n + 1));
+    int *lci = xmalloc(sizeof(int) * (size_t)(srp[n] > 0 ? srp[n] : 1));
+    lrp[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t o = lrp[i];
+        for (int64_t k = srp[i]; k < srp[i + 1]; ++k)
+            if (sub[sci[k]] == sub[i]) lci[o++] = sci[k];
+        lrp[i + 1] = o;
+    }
+    int *first = rs_coarsen(n, lrp, lci);
+    free(lrp);
+    free(lci);
+    /* 2. interior C points of the first pass */
+    int64_t *trp;
+    int *tci;
+    pattern_transpose(n, srp, sci, &trp, &tci);
+    int *state = xcalloc((size_t)n, sizeof(int));
+    for (int i = 0; i < n; ++i) {
+        int interior = 1;
+        for (int64_t k = srp[i]; k < srp[i + 1] && interior; ++k) interior = sub[sci[k]] == sub[i];
+        for (int64_t k = trp[i]; k < trp[i + 1] && interior; ++k) interior = sub[tci[k]] == sub[i];
+        if (interior && first[i] == 1) state[i] = 1;
+    }
+    free(first);
+    /* 3. PMIS */
+    uint64_t *draw = xmalloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) draw[i] = splitmix64(((uint64_t)level << 40) + (uint64_t)i);
+    for (int i = 0; i < n; ++i)
+        if (state[i] == 0 && trp[i + 1] == trp[i]) state[i] = 2;
+    int *pick = xcalloc((size_t)n, sizeof(int));
+    for (;;) {
+        for (int i = 0; i < n; ++i) {
+            if (state[i] != 0) continue;
+            for (int64_t k = srp[i]; k < srp[i + 1]; ++k)
+                if (state[sci[k]] == 1) { state[i] = 2; break; }
+        }
+        int left = 0;
+        for (int i = 0; i < n; ++i) left += state[i] == 0;
+        if (left == 0) break;
+        for (int i = 0; i < n; ++i) {
+            pick[i] = 0;
+            if (state[i] != 0) continue;
+            int first_among = 1;
+            for (int64_t k = srp[i]; k < srp[i + 1] && first_among; ++k) {
+                int j = sci[k];
+                if (j != i && state[j] == 0 && pmis_before(j, i, trp, draw)) first_among = 0;
+            }
+            for (int64_t k = trp[i]; k < trp[i + 1] && first_among; ++k) {
+                int j = tci[k];
+                if (j != i && state[j] == 0 && pmis_before(j, i, trp, draw)) first_among = 0;
+            }
+            pick[i] = first_among;
+        }
+        for (int i = 0; i < n; ++i)
+            if (pick[i]) state[i] = 1;
+    }
+    free(pick);
+    free(draw);
     free(trp);
     free(tci);
     return state;
@@ -626,11 +733,15 @@ static void mat_copy_in(Mat *M, int n, const int64_t *rp, const int *ci, const d
  * A_{l+1} = R_l A_l P_l until n_l <= max_coarse, max_levels levels exist, or
  * the split keeps more than 90% of the points (Section 2). */
 void *orc_hier_build(int n, const int64_t *rp, const int *ci, const double *v, double theta,
-                     int max_coarse, int max_levels, int interp, int pmax)
+                     int max_coarse, int max_levels, int interp, int pmax, int coarsen, const int *part)
 {
     Hier *H = xcalloc(1, sizeof(Hier));
     if (max_levels > ORC_MAXLEV) max_levels = ORC_MAXLEV;
     mat_copy_in(&H->A[0], n, rp, ci, v);
+    /* subdomain of every point of the current level (HMIS): level 0 from
+     * part, a C point keeps the subdomain of the fine point it comes from */
+    int *sub = xmalloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) sub[i] = part ? part[i] : 0;
     int l = 0;
     for (;;) {
         Mat *A = &H->A[l];
@@ -639,7 +750,7 @@ void *orc_hier_build(int n, const int64_t *rp, const int *ci, const double *v, d
         int64_t *srp;
         int *sci;
         strength(A, theta, &srp, &sci);
-        int *state = rs_coarsen(A->n, srp, sci);
+        int *state = coarsen == 1 ? hmis_coarsen(A->n, srp, sci, sub, l) : rs_coarsen(A->n, srp, sci);
         int nc = 0;
         for (int i = 0; i < A->n; ++i) nc += (state[i] == 1);
         if (nc == 0 || (int64_t)nc * 10 > (int64_t)A->n * 9) {
@@ -657,11 +768,17 @@ void *orc_hier_build(int n, const int64_t *rp, const int *ci, const double *v, d
         else direct_interp(A, srp, sci, state, cmap, nc, &H->P[l]);
         transpose(&H->P[l], &H->R[l]);
         galerkin(&H->R[l], A, &H->P[l], &H->A[l + 1]);
+        int *subc = xmalloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+        for (int i = 0; i < A->n; ++i)
+            if (cf[i]) subc[cmap[i]] = sub[i];
+        free(sub);
+        sub = subc;
         H->cf[l] = cf;
         H->cmap[l] = cmap;
         free(srp); free(sci); free(state);
         ++l;
     }
+    free(sub);
     H->nlev = l + 1;
     int nL = H->A[l].n;
     if (nL > ORC_MAX_COARSE_DENSE) {     /* a dense inverse would not fit */

@@ -47,7 +47,7 @@ def oracle_lib():
         vp = C.c_void_p
         sig = {
             "orc_hier_build": (vp, [C.c_int, i64p, i32p, f64p, C.c_double, C.c_int, C.c_int, C.c_int,
-                                    C.c_int]),
+                                    C.c_int, C.c_int, i32p]),
             "orc_hier_free": (None, [vp]),
             "orc_hier_status": (C.c_int, [vp]),
             "orc_hier_nlev": (C.c_int, [vp]),
@@ -103,7 +103,7 @@ class Oracle:
     """
 
     def __init__(self, rowptr, col, val, part=None, nsub=1, padding=1,
-                 theta=0.25, max_coarse=16, max_levels=25, interp="direct", pmax=4):
+                 theta=0.25, max_coarse=16, max_levels=25, interp="direct", pmax=4, coarsen="rs"):
         lib = oracle_lib()
         self.lib = lib
         self.h = None
@@ -114,8 +114,13 @@ class Oracle:
         self.n = len(rp) - 1
         if interp not in ("direct", "exti"):
             raise ValueError("interp is 'direct' or 'exti' (extended+i)")
+        if coarsen not in ("rs", "hmis"):
+            raise ValueError("coarsen is 'rs' (Ruge-Stueben first pass) or 'hmis'")
+        # HMIS coarsens within the subdomains first; without a partition it
+        # sees one subdomain
+        sub = np.zeros(self.n, np.int32) if part is None else np.ascontiguousarray(part, dtype=np.int32)
         self.h = lib.orc_hier_build(self.n, rp, ci, v, float(theta), int(max_coarse), int(max_levels),
-                                    1 if interp == "exti" else 0, int(pmax))
+                                    1 if interp == "exti" else 0, int(pmax), 1 if coarsen == "hmis" else 0, sub)
         st = lib.orc_hier_status(self.h)
         if st != 0:
             lib.orc_hier_free(self.h)

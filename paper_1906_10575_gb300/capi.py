@@ -36,7 +36,7 @@ class amgdd_options(C.Structure):
                 ("n_fac", C.c_int32), ("strict_assumption", C.c_int32), ("host_only", C.c_int32),
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("precision", C.c_int32),
                 ("hybrid_level", C.c_int32), ("interp", C.c_int32), ("p_max", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("coarsen", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class amgdd_setup_stats(C.Structure):

@@ -41,6 +41,8 @@ struct HierarchyParams {
     int max_levels = 25;
     int interp = 0;       // 0 direct, 1 extended+i
     int p_max = 4;        // extended+i truncation (0 = none)
+    int coarsen = 0;      // 0 Ruge-Stueben first pass, 1 HMIS over the subdomains
+    const int32_t *part = nullptr;   // subdomain of every level-0 point (HMIS)
 };
 
 // Returns an empty string on success, else the reason.

@@ -561,6 +561,7 @@ amgdd_status amgdd_options_default(amgdd_options *o)
     o->interp = 0;
     o->p_max = 4;
     o->hybrid_level = 0;
+    o->coarsen = 0;
     return AMGDD_OK;
 }
 
@@ -619,7 +620,7 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
     else amgdd_options_default(&h->opt);
     if (h->opt.n_fac < 1 || h->opt.max_levels < 1 || h->opt.max_coarse < 1 || !(h->opt.theta > 0.0) ||
         !(h->opt.theta <= 1.0) || h->opt.precision < 0 || h->opt.precision > 1 || h->opt.interp < 0 ||
-        h->opt.interp > 1 || h->opt.p_max < 0) {
+        h->opt.interp > 1 || h->opt.p_max < 0 || h->opt.coarsen < 0 || h->opt.coarsen > 1) {
         delete h;
         return fail(nullptr, AMGDD_ERR_INVALID_ARG, "options out of range");
     }
@@ -640,6 +641,8 @@ amgdd_status amgdd_setup(const amgdd_csr *A, const int32_t *part, int32_t nsub, 
         prm.max_levels = std::min(h->opt.max_levels, (int32_t)AMGDD_MAX_LEVELS);
         prm.interp = h->opt.interp;
         prm.p_max = h->opt.p_max;
+        prm.coarsen = h->opt.coarsen;
+        prm.part = part;
         int hst = 0;
         why = build_hierarchy(A0, prm, h->H, hst);
         if (hst != 0) {

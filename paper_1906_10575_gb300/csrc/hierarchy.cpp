@@ -10,6 +10,7 @@
 //                 lambda_i = |S_i^T n U| + 2 |S_i^T n F| (smallest index on a
 //                 tie), make it C and the undecided points depending on it F;
 //                 points with no strong connection either way start as F;
+//                 or (option) HMIS over the subdomains, stated at hmis_split;
 //   * interp.   : F point i, strong C neighbours C_i, ascending sums
 //                 alpha = sum_{j != i, a_ij < 0} a_ij / sum_{k in C_i} a_ik,
 //                 d = a_ii + sum_{j != i, a_ij > 0} a_ij,  w_ik = (-alpha a_ik) / d;
@@ -139,6 +140,87 @@ std::vector<uint8_t> first_pass_split(const Pattern &S, const Pattern &St, int32
             const int32_t j = S.idx[a];
             if (st[j] == kU) { key[j] -= 1; T.refresh(j); }
         }
+    }
+    std::vector<uint8_t> isC((size_t)n);
+    for (int32_t i = 0; i < n; ++i) isC[i] = (st[i] == kC);
+    return isC;
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output for counter x; the
+// reproducible stand-in for the random part of the PMIS measure.
+uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// HMIS splitting (De Sterck, Yang and Heys 2006; the coarsening of the hypre
+// defaults the paper runs with) with the subdomains as the processors: the
+// first pass on each subdomain's own strong connections; its C points at
+// interior points (every strong connection, either direction, inside the
+// subdomain) start PMIS on the whole strength graph, whose measure |S_i^T| is
+// tie-broken by splitmix64((level << 40) + i), then by the smaller index.
+// Returns 1 for C, 0 for F.
+std::vector<uint8_t> hmis_split(const Pattern &S, const Pattern &St, int32_t n, const std::vector<int32_t> &sub,
+                                int level)
+{
+    Pattern Sl;
+    Sl.ptr.assign((size_t)n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t k = S.ptr[i]; k < S.ptr[i + 1]; ++k)
+            if (sub[S.idx[k]] == sub[i]) Sl.idx.push_back(S.idx[k]);
+        Sl.ptr[i + 1] = (int64_t)Sl.idx.size();
+    }
+    const std::vector<uint8_t> first = first_pass_split(Sl, transpose_pattern(Sl, n), n);
+    enum : int8_t { kU = 0, kC = 1, kF = 2 };
+    std::vector<int8_t> st((size_t)n, kU);
+    for (int32_t i = 0; i < n; ++i) {
+        bool interior = true;
+        for (int64_t k = S.ptr[i]; k < S.ptr[i + 1] && interior; ++k) interior = sub[S.idx[k]] == sub[i];
+        for (int64_t k = St.ptr[i]; k < St.ptr[i + 1] && interior; ++k) interior = sub[St.idx[k]] == sub[i];
+        if (interior && first[i]) st[i] = kC;
+    }
+    std::vector<uint64_t> draw((size_t)n);
+    for (int32_t i = 0; i < n; ++i) draw[i] = splitmix64(((uint64_t)level << 40) + (uint64_t)i);
+    auto before = [&](int32_t i, int32_t j) {   // i ahead of j in the PMIS order
+        const int64_t ci = St.ptr[i + 1] - St.ptr[i], cj = St.ptr[j + 1] - St.ptr[j];
+        if (ci != cj) return ci > cj;
+        if (draw[i] != draw[j]) return draw[i] > draw[j];
+        return i < j;
+    };
+    for (int32_t i = 0; i < n; ++i)
+        if (st[i] == kU && St.ptr[i + 1] == St.ptr[i]) st[i] = kF;
+    std::vector<uint8_t> pick((size_t)n, 0);
+    for (;;) {
+        int64_t left = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            if (st[i] != kU) continue;
+            for (int64_t k = S.ptr[i]; k < S.ptr[i + 1]; ++k)
+                if (st[S.idx[k]] == kC) {
+                    st[i] = kF;
+                    break;
+                }
+            left += st[i] == kU;
+        }
+        if (left == 0) break;
+        for (int32_t i = 0; i < n; ++i) {
+            pick[i] = 0;
+            if (st[i] != kU) continue;
+            bool ahead = true;
+            for (int64_t k = S.ptr[i]; k < S.ptr[i + 1] && ahead; ++k) {
+                const int32_t j = S.idx[k];
+                if (j != i && st[j] == kU && before(j, i)) ahead = false;
+            }
+            for (int64_t k = St.ptr[i]; k < St.ptr[i + 1] && ahead; ++k) {
+                const int32_t j = St.idx[k];
+                if (j != i && st[j] == kU && before(j, i)) ahead = false;
+            }
+            pick[i] = ahead;
+        }
+        for (int32_t i = 0; i < n; ++i)
+            if (pick[i]) st[i] = kC;
     }
     std::vector<uint8_t> isC((size_t)n);
     for (int32_t i = 0; i < n; ++i) isC[i] = (st[i] == kC);
@@ -422,13 +504,18 @@ std::string build_hierarchy(const Csr &A0, const HierarchyParams &prm, Hierarchy
     H.lv.emplace_back();
     H.lv[0].A = A0;
     const int max_levels = std::min(prm.max_levels, 40);
+    // subdomain of every point of the current level (HMIS): level 0 from the
+    // partition, a C point keeps the subdomain of the fine point it comes from
+    std::vector<int32_t> sub((size_t)A0.rows, 0);
+    if (prm.part) sub.assign(prm.part, prm.part + A0.rows);
     for (int l = 0;; ++l) {
         HLevel &cur = H.lv[l];
         cur.l1inv = l1_inverse(cur.A);
         if (l + 1 >= max_levels || cur.A.rows <= prm.max_coarse) break;
         Pattern S = strong_connections(cur.A, prm.theta);
         Pattern St = transpose_pattern(S, cur.A.rows);
-        std::vector<uint8_t> isC = first_pass_split(S, St, cur.A.rows);
+        std::vector<uint8_t> isC = prm.coarsen == 1 ? hmis_split(S, St, cur.A.rows, sub, l)
+                                                    : first_pass_split(S, St, cur.A.rows);
         int64_t nc = 0;
         for (uint8_t c : isC) nc += c;
         if (nc == 0 || nc * 10 > (int64_t)cur.A.rows * 9) break;
@@ -441,6 +528,10 @@ std::string build_hierarchy(const Csr &A0, const HierarchyParams &prm, Hierarchy
                                 : direct_interpolation(cur.A, S, isC, coarse, (int32_t)nc);
         cur.R = transpose(cur.P);
         nxt.A = galerkin_product(cur.R, cur.A, cur.P);
+        std::vector<int32_t> subc((size_t)nc);
+        for (int32_t i = 0; i < cur.A.rows; ++i)
+            if (isC[i]) subc[coarse[i]] = sub[i];
+        sub.swap(subc);
         cur.isC = std::move(isC);
         cur.coarse = std::move(coarse);
         H.lv.push_back(std::move(nxt));

@@ -52,13 +52,15 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("interp,pmax", [("direct", 4), ("exti", 4), ("exti", 0)])
+@pytest.mark.parametrize("coarsen,interp,pmax", [("rs", "direct", 4), ("rs", "exti", 4), ("rs", "exti", 0),
+                                                  ("hmis", "direct", 4), ("hmis", "exti", 4)])
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
-def test_hierarchy_and_maps_bit_exact(name, make, interp, pmax):
-    """Direct and extended+i interpolation (truncated to 4 or untruncated)."""
+def test_hierarchy_and_maps_bit_exact(name, make, coarsen, interp, pmax):
+    """Ruge-Stueben first pass or HMIS over the subdomains; direct and
+    extended+i interpolation (truncated to 4 or untruncated)."""
     rp, ci, v, part, nsub, pad = make()
-    o = Oracle(rp, ci, v, part, nsub, pad, interp=interp, pmax=pmax)
-    s = Solver(rp, ci, v, part, nsub, pad, host_only=True, interp=interp, p_max=pmax)
+    o = Oracle(rp, ci, v, part, nsub, pad, interp=interp, pmax=pmax, coarsen=coarsen)
+    s = Solver(rp, ci, v, part, nsub, pad, host_only=True, interp=interp, p_max=pmax, coarsen=coarsen)
     assert s.level_n == o.level_n
     for l in range(o.nlev):
         for which in ("A", "P", "R"):

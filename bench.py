@@ -214,7 +214,8 @@ def run_reference(args, w):
     """CPU oracle arm: each step is one AMG-DD iteration on all host cores."""
     from oracle import Oracle
     cores = os.cpu_count()
-    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], interp=args.interp)
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"],
+               interp=args.interp, coarsen=args.coarsen)
     b = w["b"]
     # iterations to 1e-8 (identical on every implementation of the same arithmetic)
     t0 = time.perf_counter()
@@ -235,7 +236,8 @@ def run_reference(args, w):
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(per_iter, 3), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(_config(w), interp=args.interp),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(_config(w), interp=args.interp, coarsen=args.coarsen),
         "iterations": iters, "full_solve_ms": round(full, 1),
         "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": cores, "kind": "oracle",
                          "sample": "one AMG-DD iteration over all 512 composite grids per step "
@@ -257,13 +259,13 @@ def max_over_ranks(values, dist=None):
     return [float(v) for v in t.cpu()]
 
 
-def cpu_baseline(w, iters, interp="direct"):
+def cpu_baseline(w, iters, interp="direct", coarsen="rs"):
     """Oracle timed on a bounded sample: one full AMG-DD iteration (residual,
     restriction and AlgFAC on every composite grid, OpenMP over grids), scaled
     by the iterations to 1e-8."""
     from oracle import Oracle
     cores = os.cpu_count()
-    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], interp=interp)
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], interp=interp, coarsen=coarsen)
     b = w["b"]
     t0 = time.perf_counter()
     o.amgdd_iteration(b, np.zeros(o.n), w["n_fac"])
@@ -316,7 +318,8 @@ def run_extra(args, name, stream, dist, local):
     prec = int(w.get("precision", 0))
     maxit = 2000
     t0 = time.perf_counter()
-    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+               interp=args.interp, coarsen=args.coarsen,
                precision=prec, schedule=args.schedule, stream=stream,
                max_coarse=16 * (len(w["edges"]) if multi else 1))
     setup_s = time.perf_counter() - t0
@@ -404,7 +407,8 @@ def run_extra(args, name, stream, dist, local):
     err = None
     if not multi and prec == 1 and not args.no_fp64_check:
         # FP64 AMG-DD on the same problem: reference solution for the error
-        s64 = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
+        s64 = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                     interp=args.interp, coarsen=args.coarsen,
                      stream=stream)
         x64 = torch.zeros(n, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
@@ -436,7 +440,8 @@ def run_extra(args, name, stream, dist, local):
         "data": "synthetic",
         "config": {"workload": desc, "n": n, "nnz": int(len(w["col"])), "nsub": int(w["nsub"]), "nrhs": nrhs,
                    "l2_policy": ("L2-resident problem; 256 MB written before every timed solve" if small
-                                 else "inputs larger than L2"), "interp": args.interp},
+                                 else "inputs larger than L2"), "interp": args.interp,
+                   "coarsen": args.coarsen},
         "iterations": it, "final_relres": info["final_relres"],
         "vcycle_fp64": {"ms_all_columns": round(v_ms, 3), "iterations": v_it},
         "amgdd_over_vcycle_time": round(ms / v_ms, 3),
@@ -476,7 +481,7 @@ def run_adjoint(args, stream):
     rp, ci, v = I.diffusion3d(kappa)
     part, nsub = I.box_partition((n, n, n), (16, 16, 16))
     t0 = time.perf_counter()
-    s = Solver(rp, ci, v, part, nsub, 2, n_fac=2, stream=stream, interp=args.interp)
+    s = Solver(rp, ci, v, part, nsub, 2, n_fac=2, stream=stream, interp=args.interp, coarsen=args.coarsen)
     setup_s = time.perf_counter() - t0
     if not args.no_autotune:
         capi.amgdd_autotune(s.h, 1, reps=2, stream=stream)
@@ -506,7 +511,7 @@ def run_adjoint(args, stream):
     hbm, peak_kind = _peaks()
     ms_g = statistics.median(gk)
     grad_bytes = 32.0 * n ** 3
-    o = Oracle(rp, ci, v, part, nsub, 2, interp=args.interp)
+    o = Oracle(rp, ci, v, part, nsub, 2, interp=args.interp, coarsen=args.coarsen)
     t0 = time.perf_counter()
     xo, ho = o.amgdd_solve(b, 2, tol=tol, maxit=200)
     lo, _ = o.amgdd_solve(xo - xt, 2, tol=tol, maxit=200)
@@ -521,7 +526,7 @@ def run_adjoint(args, stream):
         "data": "synthetic",
         "config": {"workload": "3D 7-point diffusion 96^3, kappa = exp(Gaussian random field, length 0.1, "
                                "variance 1) seed 0, 216 subdomains of 16^3, padding 2, loss 1/2|x - x_t|^2, "
-                               "solves to 1e-10", "interp": args.interp},
+                               "solves to 1e-10", "interp": args.interp, "coarsen": args.coarsen},
         "forward_ms": round(statistics.median(fw), 3), "forward_iterations": i1["iterations"],
         "adjoint_ms": round(statistics.median(bw), 3), "adjoint_iterations": i2["iterations"],
         "gradient_kernel_ms": round(ms_g, 4),
@@ -562,6 +567,9 @@ def main():
     ap.add_argument("--interp", default="direct", choices=["direct", "exti"],
                     help="interpolation of the hierarchy: direct (default) or extended+i, "
                          "truncated to 4 entries per row")
+    ap.add_argument("--coarsen", default="rs", choices=["rs", "hmis"],
+                    help="C/F splitting of the hierarchy: rs (default, Ruge-Stueben first pass) or hmis "
+                         "(over the subdomains)")
     ap.add_argument("--candidate", type=int, default=-1,
                     help="use this FAC kernel candidate instead of autotuning (profiling captures)")
     ap.add_argument("--edge", type=int, default=0,
@@ -605,7 +613,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
-    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+               interp=args.interp, coarsen=args.coarsen,
                schedule=args.schedule, stream=stream)
     st = s.stats
     b = torch.from_numpy(w["b"]).cuda()
@@ -703,7 +712,8 @@ def main():
     mixed = None
     if not args.no_mixed:
         s.close()
-        sm = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
+        sm = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                    interp=args.interp, coarsen=args.coarsen,
                     precision=1, stream=stream)
         cand_m = None
         if not args.no_autotune:
@@ -750,7 +760,8 @@ def main():
     # cycle on level --hybrid-level
     hybrid = None
     if args.hybrid_level > 0:
-        sh = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
+        sh = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                    interp=args.interp, coarsen=args.coarsen,
                     hybrid_level=args.hybrid_level, stream=stream)
         with torch.cuda.stream(stream):
             timed(sh.hybrid_solve, args.warmup)
@@ -764,7 +775,8 @@ def main():
     # entry feeds four fma chains
     multi = None
     if not args.no_multi:
-        sq = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"], interp=args.interp,
+        sq = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], n_fac=w["n_fac"],
+                    interp=args.interp, coarsen=args.coarsen,
                     stream=stream)
         Bm = torch.from_numpy(np.ascontiguousarray(np.stack([I.uniform_rhs(sq.n, j) for j in range(4)], 1))).cuda()
         Xm = torch.zeros_like(Bm)
@@ -839,7 +851,7 @@ def main():
         "metric": METRIC, "value": round(ms_dd, 3), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_dd, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(_config(w), interp=args.interp),
+        "data": "synthetic", "config": dict(_config(w), interp=args.interp, coarsen=args.coarsen),
         "iterations": it_dd, "final_relres": i_dd[-1]["final_relres"],
         "gbs": round(dd_bytes / (ms_dd * 1e-3) / 1e9, 1),
         "vcycle": {"ms": round(ms_v, 3), "iterations": it_v, "final_relres": i_v[-1]["final_relres"],
@@ -861,7 +873,7 @@ def main():
         "hybrid": hybrid,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, it_dd, args.interp)
+        line["cpu_baseline"] = cpu_baseline(w, it_dd, args.interp, args.coarsen)
     if rank == 0:
         print(json.dumps(line))
     if s.h:

@@ -113,6 +113,9 @@ def test_validation_errors():
     with pytest.raises(capi.AmgddError) as e:
         Solver(rp, ci2, v, part, nsub, 1, host_only=True)
     assert e.value.status == 1
+    with pytest.raises(capi.AmgddError) as e:       # coarsening option out of range
+        Solver(rp, ci, v, part, nsub, 1, host_only=True, coarsen=2)
+    assert e.value.status == 1
     s = Solver(rp, ci, v, part, nsub, 1, host_only=True)
     with pytest.raises(capi.AmgddError) as e:       # no device side
         capi.amgdd_iterate(s.h, None, None)

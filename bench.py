@@ -42,8 +42,8 @@ def _config(w):
     n = int(len(w["rowptr"]) - 1)
     e = w["shape"][0]
     return {
-        "workload": "3D 7-point Poisson %d^3 (N=%d), %d subdomains of 16^3, padding 2, "
-                    "2 AlgFAC V(1,1) per iteration, FP64, b~U[-1,1] seed 0, x0=0" % (e, n, w["nsub"]),
+        "workload": "3D 7-point Poisson %d^3 (N=%d), %d subdomains of 16^3, padding %d, "
+                    "2 AlgFAC V(1,1) per iteration, FP64, b~U[-1,1] seed 0, x0=0" % (e, n, w["nsub"], w["padding"]),
         "n": n, "nnz": int(len(w["col"])), "nsub": int(w["nsub"]),
         "padding": int(w["padding"]), "n_fac": int(w["n_fac"]), "tol": TOL,
         "l2_policy": "inputs larger than L2 (composite operators 7 GB, fine matrix 183 MB)",
@@ -311,6 +311,8 @@ def run_extra(args, name, stream, dist, local):
 
     shape = (args.edge, args.edge) if name == "poisson2d_64" and args.edge > 0 else None
     w = I.workload(name, seed=0, nsys=args.nsys if "nsys" in I.WORKLOADS[name] else None, shape=shape)
+    if args.padding >= 0:
+        w["padding"] = args.padding
     n = int(len(w["rowptr"]) - 1)
     hbm, peak_kind = _peaks()
     multi = "nsys" in I.WORKLOADS[name]
@@ -421,18 +423,19 @@ def run_extra(args, name, stream, dist, local):
     it = info["iterations"]
     if multi:
         desc = ("%d independent 3D 7-point Poisson systems (edges %s drawn from {32,48,64,80,96}, N=%d total), "
-                "boxes of 16^3 (%d subdomains), padding 2, %d right-hand sides U[-1,1], "
+                "boxes of 16^3 (%d subdomains), padding %d, %d right-hand sides U[-1,1], "
                 "FP32 AlgFAC / FP64 refinement" % (len(w["edges"]), ",".join(map(str, sorted(set(w["edges"])))),
-                                                     n, w["nsub"], nrhs))
+                                                     n, w["nsub"], w["padding"], nrhs))
     elif small:
-        desc = ("2D 5-point Poisson %d^2 (N=%d), %d subdomains of 16^2, padding 1, 2 AlgFAC V(1,1) per "
-                "iteration, FP64, b~U[-1,1] seed 0, x0=0" % (w["shape"][0], n, w["nsub"]))
+        desc = ("2D 5-point Poisson %d^2 (N=%d), %d subdomains of 16^2, padding %d, 2 AlgFAC V(1,1) per "
+                "iteration, FP64, b~U[-1,1] seed 0, x0=0" % (w["shape"][0], n, w["nsub"], w["padding"]))
     elif "aniso" in I.WORKLOADS[name]:
         desc = ("2D rotated anisotropic diffusion theta=3pi/16, eps=1e-3, 9-point, 512^2 (N=%d), %d subdomains "
-                "of 32^2, padding 2, FP64, b~U[-1,1] seed 0" % (n, w["nsub"]))
+                "of 32^2, padding %d, FP64, b~U[-1,1] seed 0" % (n, w["nsub"], w["padding"]))
     else:
         desc = ("3D 7-point diffusion 256^3 (N=%d), kappa on 8^3 blocks of 32^3 i.i.d. {1,1e3}, %d subdomains "
-                "of 16^3, padding 2, FP32 AlgFAC / FP64 refinement, b~U[-1,1] seed 0" % (n, w["nsub"]))
+                "of 16^3, padding %d, FP32 AlgFAC / FP64 refinement, b~U[-1,1] seed 0" % (n, w["nsub"],
+                                                                                          w["padding"]))
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": False,
@@ -567,6 +570,9 @@ def main():
     ap.add_argument("--interp", default="direct", choices=["direct", "exti"],
                     help="interpolation of the hierarchy: direct (default) or extended+i, "
                          "truncated to 4 entries per row")
+    ap.add_argument("--padding", type=int, default=-1,
+                    help="padding eta on every level instead of the workload's (-1, the default, keeps "
+                         "it; not for adjoint_96)")
     ap.add_argument("--coarsen", default="rs", choices=["rs", "hmis"],
                     help="C/F splitting of the hierarchy: rs (default, Ruge-Stueben first pass) or hmis "
                          "(over the subdomains)")
@@ -598,6 +604,8 @@ def main():
             run_extra(args, args.workload, torch.cuda.Stream(), None, local)
         return
     w = I.workload(WORKLOAD, seed=0, shape=(args.n,) * 3)
+    if args.padding >= 0:
+        w["padding"] = args.padding
 
     if args.impl == "reference":
         if rank == 0:

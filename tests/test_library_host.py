@@ -136,8 +136,8 @@ def test_hybrid_layouts_validate_on_host():
     assert e.value.status == 1
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_streamed_layout_matches_whole_layout(precision):
+@pytest.mark.parametrize("precision,coarsen", [(0, "rs"), (1, "rs"), (0, "hmis")])
+def test_streamed_layout_matches_whole_layout(precision, coarsen):
     """A device setup packs the composite-grid layout in chunks of grids and
     drops each chunk once it is checked and copied; host_only = 3 runs that
     same streamed packing and its per-chunk range checks without a GPU. With
@@ -145,8 +145,8 @@ def test_streamed_layout_matches_whole_layout(precision):
     layout agree in every per-level entry count and in the FMA count."""
     rp, ci, v = I.poisson3d(40, 40, 40)
     part, nsub = I.box_partition((40, 40, 40), (5, 5, 5))
-    whole = Solver(rp, ci, v, part, nsub, 2, host_only=2, precision=precision)
-    streamed = Solver(rp, ci, v, part, nsub, 2, host_only=3, precision=precision)
+    whole = Solver(rp, ci, v, part, nsub, 2, host_only=2, precision=precision, coarsen=coarsen)
+    streamed = Solver(rp, ci, v, part, nsub, 2, host_only=3, precision=precision, coarsen=coarsen)
     a, b = whole.stats, streamed.stats
     assert a.fac_fma == b.fac_fma > 0
     assert a.fac_entry_bytes == b.fac_entry_bytes == (6 if precision else 10)
@@ -165,6 +165,10 @@ def test_streamed_layout_uneven_batch():
     rp, ci, v, part, nsub, B, picks, offs = I.batched_poisson(3, edges=(18, 24, 30), box=8, nrhs=1, seed=3)
     assert len(rp) - 1 == offs[-1] and nsub == sum(-(-e // 8) ** 3 for e in picks)
     s = Solver(rp, ci, v, part, nsub, 2, host_only=3, precision=1, hybrid_level=1)
+    assert s.stats.fac_fma > 0
+    s.close()
+    # the same with HMIS: its composite grids pass the device-index checks too
+    s = Solver(rp, ci, v, part, nsub, 2, host_only=3, precision=1, hybrid_level=1, coarsen="hmis")
     assert s.stats.fac_fma > 0
     s.close()
 

@@ -223,3 +223,26 @@ def test_device_entry_points_refuse_host_only_handles():
         with pytest.raises(capi.AmgddError) as e:
             Solver(rp, ci, v, part, nsub, 1, host_only=True, **kw)
         assert e.value.status == 1, kw
+
+
+@pytest.mark.slow
+def test_hmis_exti_hierarchy_and_maps_bit_exact_at_128cubed():
+    """The paper's hierarchy flavour (HMIS over the 512 subdomains, extended+i
+    truncated to 4) at the full size of the 128^3 benchmark workload: every
+    level's operators and every composite grid's maps equal the oracle's."""
+    w = I.workload("poisson3d_128")
+    o = Oracle(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], coarsen="hmis", interp="exti")
+    s = Solver(w["rowptr"], w["col"], w["val"], w["part"], w["nsub"], w["padding"], host_only=1, coarsen="hmis",
+               interp="exti")
+    assert s.level_n == o.level_n
+    for l in range(o.nlev):
+        for which in ("A", "P", "R") if l < o.nlev - 1 else ("A",):
+            a, b = o.matrix(l, which), capi.amgdd_get_operator(s.h, l, which)
+            assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])), (l, which)
+    for p in range(w["nsub"]):
+        for l in range(o.nlev):
+            g1, k1 = o.comp_map(p, l)
+            g2, k2 = capi.amgdd_get_maps(s.h, p, l)
+            assert np.array_equal(g1, g2) and np.array_equal(k1, k2), (p, l)
+    assert s.stats.assumption_violations == o.violations() == 0
+    s.close()

@@ -36,6 +36,43 @@ def test_library_exports_every_declared_symbol():
     assert sorted(capi.EXPORTS) == names
 
 
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    that a C compiler gives the header's structs, and the constants agree
+    (status codes, AMGDD_MAX_LEVELS, AMGDD_FAC_CANDIDATES, tuning flag)."""
+    import ctypes
+    import subprocess
+    structs = {"amgdd_csr": capi.amgdd_csr, "amgdd_options": capi.amgdd_options,
+               "amgdd_setup_stats": capi.amgdd_setup_stats, "amgdd_solve_info": capi.amgdd_solve_info}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "amgdd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    consts = {"AMGDD_MAX_LEVELS": capi.MAX_LEVELS, "AMGDD_FAC_CANDIDATES": capi.FAC_CANDIDATES,
+              "AMGDD_TUNE_ALLOW_REORDERED": capi.TUNE_ALLOW_REORDERED}
+    consts.update({v: k for k, v in capi.STATUS.items()})
+    for c in consts:
+        lines.append('printf("const %s %%d\\n", (int)%s);' % (c, c))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            a, b, c = ln.split()
+            got[(a, b)] = int(c)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+    for c, v in consts.items():
+        assert got[("const", c)] == v, c
+
+
 def _pair(rp, ci, v, part, nsub, pad, **kw):
     o = Oracle(rp, ci, v, part, nsub, pad, **kw)
     s = Solver(rp, ci, v, part, nsub, pad, host_only=True, **kw)

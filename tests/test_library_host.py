@@ -73,6 +73,42 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
         assert got[("const", c)] == v, c
 
 
+def _header_signatures():
+    """name -> list of parameter kinds ('p' pointer, 'i32', 'i64', 'f64') of
+    every function include/amgdd.h declares."""
+    txt = open(os.path.join(ROOT, "include", "amgdd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(amgdd_\w+|amg_\w+)\s*\(([^)]*)\)\s*;", txt):
+        kinds = []
+        for prm in [q.strip() for q in m.group(2).split(",") if q.strip() and q.strip() != "void"]:
+            if "*" in prm or prm.startswith("amgdd_handle"):
+                kinds.append("p")
+            elif prm.startswith("int32_t"):
+                kinds.append("i32")
+            elif prm.startswith("int64_t"):
+                kinds.append("i64")
+            elif prm.startswith("double"):
+                kinds.append("f64")
+            else:
+                raise AssertionError("unclassified parameter %r of %s" % (prm, m.group(1)))
+        out[m.group(1)] = kinds
+    return out
+
+
+def test_binding_argument_types_match_the_header():
+    """Every declared function is bound with as many arguments as the header
+    gives it, each of the same kind (pointer, 32- or 64-bit integer, double)."""
+    import ctypes
+    lib = capi.load()
+    kind = {ctypes.c_int32: "i32", ctypes.c_int64: "i64", ctypes.c_double: "f64"}
+    sigs = _header_signatures()
+    assert sorted(sigs) == sorted(capi.EXPORTS)
+    for name, want in sigs.items():
+        got = [kind.get(t, "p") for t in getattr(lib, name).argtypes]
+        assert got == want, (name, got, want)
+
+
 def _pair(rp, ci, v, part, nsub, pad, **kw):
     o = Oracle(rp, ci, v, part, nsub, pad, **kw)
     s = Solver(rp, ci, v, part, nsub, pad, host_only=True, **kw)

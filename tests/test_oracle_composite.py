@@ -4,6 +4,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 import scipy.sparse as sp
 from scipy.sparse.csgraph import shortest_path
 
@@ -76,21 +77,23 @@ def _brute(o, part, nsub, eta):
     return out
 
 
-def test_composite_maps_match_bruteforce_2d():
+@pytest.mark.parametrize("coarsen,interp", [("rs", "direct"), ("hmis", "exti")])
+def test_composite_maps_match_bruteforce_2d(coarsen, interp):
     rp, ci, v = I.poisson2d(20, 18)
     part, nsub = I.box_partition((20, 18), (7, 6))
     for eta in (1, 2):
-        o = Oracle(rp, ci, v, part, nsub, eta)
+        o = Oracle(rp, ci, v, part, nsub, eta, coarsen=coarsen, interp=interp)
         ref = _brute(o, part, nsub, eta)
         for (p, l), (g, k) in ref.items():
             gg, kk = o.comp_map(p, l)
             assert np.array_equal(gg, g) and np.array_equal(kk, k), (p, l, eta)
 
 
-def test_composite_maps_match_bruteforce_3d():
+@pytest.mark.parametrize("coarsen,interp", [("rs", "direct"), ("hmis", "exti")])
+def test_composite_maps_match_bruteforce_3d(coarsen, interp):
     rp, ci, v = I.poisson3d(10, 9, 8)
     part, nsub = I.box_partition((10, 9, 8), (5, 5, 4))
-    o = Oracle(rp, ci, v, part, nsub, 2)
+    o = Oracle(rp, ci, v, part, nsub, 2, coarsen=coarsen, interp=interp)
     ref = _brute(o, part, nsub, 2)
     for (p, l), (g, k) in ref.items():
         gg, kk = o.comp_map(p, l)

@@ -13,5 +13,5 @@ for them, with box subdomains standing in for the METIS partition.
 from .generators import (  # noqa: F401
     poisson2d, poisson3d, diffusion3d, checkerboard_kappa, box_partition,
     uniform_rhs, grid_shape_of, workload, WORKLOADS, gaussian_random_field, lognormal_kappa,
-    batched_poisson, rotated_anisotropic2d,
+    batched_poisson, rotated_anisotropic2d, weak_link_chain,
 )

@@ -149,6 +149,36 @@ def rotated_anisotropic2d(nx: int, ny: int, theta: float = 3 * np.pi / 16, eps: 
     return rowptr.astype(np.int32), cidx.astype(np.int32), v
 
 
+def weak_link_chain(n_left: int = 8, n_right: int = 8, link: float = 0.25, y_diag: float = 1.0):
+    """1D chain whose middle point y = n_left is attached to its two chain
+    neighbours only through positive (weak) entries: rows away from y are
+    [-1, 2, -1] (entries towards y omitted), row y is [+link, y_diag, +link]
+    and its neighbours hold the symmetric +link. Irreducibly diagonally
+    dominant with a positive diagonal (SPD) for link < 1 and y_diag > 2 link. This is
+    the shape of the example of Section 4.2 in which a fine point has no
+    interpolation connection between two injected C points.
+    Returns rowptr, col (int32), val (float64) in CSR."""
+    n = n_left + 1 + n_right
+    y = n_left
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if j < 0 or j >= n:
+                continue
+            if i == j:
+                a = y_diag if i == y else 2.0
+            elif i == y or j == y:
+                a = link
+            else:
+                a = -1.0
+            rows.append(i)
+            cols.append(j)
+            vals.append(a)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, np.asarray(rows) + 1, 1)
+    return np.cumsum(rowptr).astype(np.int32), np.asarray(cols, np.int32), np.asarray(vals, np.float64)
+
+
 def checkerboard_kappa(n: int, blocks: int, seed: int, values=(1.0, 1e3)):
     """Piecewise-constant kappa on an n^3 grid: blocks^3 cubes, i.i.d. values."""
     rng = np.random.default_rng(seed)

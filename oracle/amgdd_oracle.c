@@ -51,6 +51,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXLEV 40
 #define ORC_MAX_COARSE_DENSE 8192
@@ -845,7 +848,8 @@ typedef struct {
 typedef struct {
     int nsub, nlev;
     CLevel *lv;                   /* [p * nlev + l] */
-    int64_t violations;           /* points that break the connectivity assumption */
+    int64_t violations;           /* grid-level pairs that break the connectivity assumption */
+    unsigned char *vflag;         /* [p * nlev + l]: 1 where pair (p, l) breaks it */
 } Comp;
 
 /* Multi-source breadth-first search to distance eta through the graph of A
@@ -912,6 +916,7 @@ void *orc_comp_build(void *h, const int *part, int nsub, const int *padding)
     C->nsub = nsub;
     C->nlev = H->nlev;
     C->lv = xcalloc((size_t)nsub * (size_t)H->nlev, sizeof(CLevel));
+    C->vflag = xcalloc((size_t)nsub * (size_t)H->nlev, 1);
     int n0 = H->A[0].n;
     /* owned sets on level 0 */
     int *cnt = xcalloc((size_t)nsub + 1, sizeof(int));
@@ -1039,6 +1044,7 @@ void *orc_comp_build(void *h, const int *part, int nsub, const int *padding)
                     fn = gn;
                 }
                 viol += bad;
+                C->vflag[(size_t)p * C->nlev + l] = (unsigned char)bad;
                 free(fr);
             }
         }
@@ -1056,10 +1062,20 @@ void orc_comp_free(void *c)
         free(C->lv[k].real); free(C->lv[k].ghost); free(C->lv[k].owned);
     }
     free(C->lv);
+    free(C->vflag);
     free(C);
 }
 
 int64_t orc_comp_violations(void *c) { return ((Comp *)c)->violations; }
+
+/* 1 when composite grid p breaks the connectivity assumption between levels
+ * l and l+1 (a point of P_l(Dbar_l) outside Dbar_{l+1} whose interpolatory
+ * sets reach a real point of a coarser level), else 0. */
+int orc_comp_violation_flag(void *c, int p, int l)
+{
+    Comp *C = c;
+    return C->vflag[(size_t)p * C->nlev + l];
+}
 
 /* what: 0 = |D_l|, 1 = |Dbar_l \ D_l|, 2 = owned count */
 int orc_comp_count(void *c, int p, int l, int what)
@@ -1748,4 +1764,17 @@ int orc_amgdd_solve(void *h, void *c, const double *b, double *x, double tol, in
     free(rl);
     free(r);
     return k;
+}
+
+/* Threads of the OpenMP loops over subdomains (timing of the CPU baseline at
+ * one thread and at all cores); returns the count now in effect. */
+int orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }

@@ -62,6 +62,7 @@ def oracle_lib():
             "orc_comp_build": (vp, [vp, i32p, C.c_int, i32p]),
             "orc_comp_free": (None, [vp]),
             "orc_comp_violations": (C.c_int64, [vp]),
+            "orc_comp_violation_flag": (C.c_int, [vp, C.c_int, C.c_int]),
             "orc_comp_count": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
             "orc_comp_get_map": (None, [vp, C.c_int, C.c_int, i32p, u8p]),
             "orc_comp_overhead": (C.c_double, [vp, vp]),
@@ -82,6 +83,7 @@ def oracle_lib():
             "orc_hybrid_solve": (C.c_int, [vp, vp, vp, C.c_int, C.c_int, f64p, f64p, C.c_double, C.c_int,
                                           f64p]),
             "orc_amgdd_iteration32": (None, [vp, vp, f64p, f64p, C.c_int, f64p]),
+            "orc_set_threads": (C.c_int, [C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -89,6 +91,12 @@ def oracle_lib():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops (0 keeps the current count);
+    returns the count in effect."""
+    return int(oracle_lib().orc_set_threads(int(n)))
 
 
 def _c64(a):
@@ -207,6 +215,12 @@ class Oracle:
 
     def violations(self):
         return int(self.lib.orc_comp_violations(self.c))
+
+    def violation_pairs(self):
+        """(subdomain, level) pairs that break the connectivity assumption of
+        Sections 4.2 and 4.5 between level l and l + 1, in order."""
+        return [(p, l) for p in range(self.nsub) for l in range(self.nlev - 1)
+                if self.lib.orc_comp_violation_flag(self.c, p, l)]
 
     def overhead(self):
         return float(self.lib.orc_comp_overhead(self.h, self.c))

@@ -15,7 +15,7 @@ class Solver:
 
     def __init__(self, rowptr, col, val, part, nsub, padding=1, n_fac=2, theta=0.25,
                  max_coarse=16, max_levels=25, host_only=False, threads=0, schedule=0, precision=0,
-                 hybrid_level=0, interp=0, p_max=4, coarsen=0, stream=None):
+                 hybrid_level=0, interp=0, p_max=4, coarsen=0, strict_assumption=0, stream=None):
         o = capi.amgdd_options_default()
         o.n_fac = n_fac
         o.theta = theta
@@ -29,6 +29,7 @@ class Solver:
         o.interp = {"direct": 0, "exti": 1}.get(interp, interp)
         o.p_max = p_max
         o.coarsen = {"rs": 0, "hmis": 1}.get(coarsen, coarsen)
+        o.strict_assumption = int(strict_assumption)
         self.n = len(rowptr) - 1
         self.h = capi.amgdd_setup(rowptr, col, val, part, nsub, padding, o, stream)
         self.stats = capi.amgdd_get_stats(self.h)

@@ -386,7 +386,9 @@ amgdd_status amgdd_kappa_grad_3d(int32_t nx, int32_t ny, int32_t nz, const doubl
  *   stream   : cudaStream_t (NULL = legacy default stream); stream-ordered,
  *              nothing is synchronised.
  * The first call on a device looks up the scratch's device address (with that
- * device current); make that first call before any stream capture. Every call
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) between calls: the kept address would be stale. Every call
  * shares the one scratch array, so calls whose kernels overlap on the GPU (on
  * different streams, or from different threads) race and must be serialised.
  * Errors: INVALID_ARG (size, null pointer), CUDA; text via amgdd_last_error(NULL). */

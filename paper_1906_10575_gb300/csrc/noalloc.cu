@@ -20,10 +20,10 @@
 
 namespace {
 
-// Rows handled by one block of the residual kernel, and the largest number of
-// blocks whose partial sums the static scratch holds: n is limited to
-// kRowsPerBlock * kMaxBlocks = 16,777,216 rows.
-constexpr int kThreads = 256;
+// Rows handled by one block of the residual kernel (four per thread), and the
+// largest number of blocks whose partial sums the static scratch holds: n is
+// limited to kRowsPerBlock * kMaxBlocks = 16,777,216 rows.
+constexpr int kThreads = 1024;
 constexpr int kRowsPerBlock = 4096;
 constexpr int kMaxBlocks = 4096;
 
@@ -39,7 +39,7 @@ double *g_partial_ptr[kMaxDevices] = {};
 
 
 // r_i = b_i - (sum_k a_ik x_k as an ascending fma chain); block partial of r^2.
-__global__ void k_residual_csr(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_residual_csr(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                const double *__restrict__ val, const double *__restrict__ b,
                                const double *__restrict__ x, double *__restrict__ r, double *__restrict__ partial)
 {
@@ -110,7 +110,9 @@ extern "C" amgdd_status amgdd_residual_csr_noalloc(int32_t n, const int32_t *row
     double *partial;
     {
         // Once per device, with that device current: the device address of the
-        // static scratch (its host-side name is only a stand-in).
+        // static scratch (its host-side name is only a stand-in). The address
+        // is kept for the life of the process, so a device reset
+        // (cudaDeviceReset) between calls is not supported.
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_partial_ptr[dev]) {
             void *p = nullptr;

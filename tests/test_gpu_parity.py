@@ -337,7 +337,8 @@ def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
     ref = [step(Bh[:, j], np.zeros(n), 2) for j in range(4)]
     b = _dev(Bh[:, 0])
     single = [0, 7] if precision else list(range(9))
-    exact = single + list(range(9, 18)) + list(range(20, 31))    # 18, 19 reorder row sums: tested below
+    several = list(range(9, 18)) + list(range(20, capi.FAC_CANDIDATES))
+    exact = single + several    # 18, 19 reorder row sums: tested below
     for k in exact:
         capi.amgdd_set_fac_kernel(s.h, 1, k)
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -345,14 +346,14 @@ def test_every_fac_kernel_candidate_is_bit_exact(case, precision):
         assert np.array_equal(_host(x), ref[0]), k
     for nrhs in (2, 4):
         B = torch.from_numpy(np.ascontiguousarray(Bh[:, :nrhs])).cuda()
-        for k in list(range(9, 18)) + list(range(20, 31)):
+        for k in several:
             capi.amgdd_set_fac_kernel(s.h, nrhs, k)
             X = torch.zeros((n, nrhs), dtype=torch.float64, device="cuda")
             capi.amgdd_iterate_multi(s.h, B, X)
             Xh = _host(X)
             for j in range(nrhs):
                 assert np.array_equal(Xh[:, j], ref[j]), (nrhs, k, j)
-    for k in ([1, 2, 3, 4, 5, 6, 8] if precision else []) + [31, -1]:
+    for k in ([1, 2, 3, 4, 5, 6, 8] if precision else []) + [capi.FAC_CANDIDATES, -1]:
         with pytest.raises(capi.AmgddError):
             capi.amgdd_set_fac_kernel(s.h, 1, k)
     with pytest.raises(capi.AmgddError):
@@ -439,3 +440,75 @@ def test_extended_i_hierarchy_solve_bit_exact(case, precision):
     xvo, hvo = o.vcycle_solve(b, tol=1e-8, maxit=400)
     assert iv["iterations"] == len(hvo) - 1 and np.array_equal(_host(xv), xvo)
     s.close()
+
+
+@pytest.mark.parametrize("interp", ["direct", "exti"])
+@pytest.mark.parametrize("case", ["poisson2d_64", "poisson3d_24", "kappa3d"])
+def test_hmis_hierarchy_bit_exact(case, interp):
+    """HMIS coarsening over the subdomains (the hierarchy of the hypre
+    defaults that Section 6 names), with direct and extended+i interpolation:
+    AlgFAC states of every grid and level, the AMG-DD solve (with the default
+    FAC kernel and with candidate 15, the benchmark's) and the V-cycle solve
+    equal the oracle's on the same hierarchy bit for bit."""
+    rp, ci, v, part, nsub, pad, b = _case(case)
+    o = Oracle(rp, ci, v, part, nsub, pad, interp=interp, pmax=4, coarsen="hmis")
+    s = Solver(rp, ci, v, part, nsub, pad, n_fac=2, interp=interp, p_max=4, coarsen="hmis")
+    assert s.level_n == o.level_n
+    rl = o.restrict_all(b)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    capi.amgdd_fac(s.h, _dev(np.concatenate(rl)), x)
+    for p in range(s.nsub):
+        uo, fo = o.algfac(p, rl, 2)
+        for l in range(s.nlev):
+            g, k = capi.amgdd_get_maps(s.h, p, l)
+            ug, fg = capi.amgdd_get_fac_state(s.h, p, l, len(g))
+            assert np.array_equal(ug, uo[l][g]), (p, l)
+            assert np.array_equal(fg[k < 2], fo[l][g[k < 2]]), (p, l)
+    assert np.array_equal(_host(x), o.amgdd_iteration(b, np.zeros(s.n), 2))
+    xo, ho = o.amgdd_solve(b, 2, tol=1e-8, maxit=300)
+    for cand in (7, 15):
+        capi.amgdd_set_fac_kernel(s.h, 1, cand)
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        info = s.solve(_dev(b), x, tol=1e-8, max_iter=300)
+        assert info["converged"] and info["iterations"] == len(ho) - 1, cand
+        assert np.array_equal(_host(x), xo), cand
+        assert np.allclose(info["history"], ho, rtol=1e-12, atol=0), cand
+    xv = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    iv = s.vcycle_solve(_dev(b), xv, tol=1e-8, max_iter=400)
+    xvo, hvo = o.vcycle_solve(b, tol=1e-8, maxit=400)
+    assert iv["iterations"] == len(hvo) - 1 and np.array_equal(_host(xv), xvo)
+    s.close()
+
+
+def test_assumption_violating_hierarchy_on_device():
+    """The hand-derived chain whose composite grids break the connectivity
+    assumption of Sections 4.2 and 4.5 (tests/golden/assumption_chain17.json):
+    with strict_assumption the device setup is refused with
+    AMGDD_ERR_HIERARCHY_ASSUMPTION and leaves no device memory behind;
+    without it, both sides drop the same points and the GPU solve equals the
+    oracle's bit for bit at padding 0, 1 and 2."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "assumption_chain17.json")))
+    rp, ci, v = I.weak_link_chain(8, 8)
+    part = np.asarray(gold["part"], np.int32)
+    nsub = gold["nsub"]
+    b = I.uniform_rhs(len(rp) - 1, 3)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        with pytest.raises(capi.AmgddError) as e:
+            Solver(rp, ci, v, part, nsub, 1, max_coarse=gold["max_coarse"], strict_assumption=1)
+        assert e.value.status == 3
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for eta in (0, 1, 2):
+        o = Oracle(rp, ci, v, part, nsub, eta, max_coarse=gold["max_coarse"])
+        s = Solver(rp, ci, v, part, nsub, eta, max_coarse=gold["max_coarse"], n_fac=2)
+        assert s.stats.assumption_violations == len(gold["violations"][str(eta)]) == o.violations()
+        x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        info = s.solve(_dev(b), x, tol=1e-8, max_iter=100)
+        xo, ho = o.amgdd_solve(b, 2, tol=1e-8, maxit=100)
+        assert info["iterations"] == len(ho) - 1, eta
+        assert np.array_equal(_host(x), xo), eta
+        s.close()

@@ -327,8 +327,15 @@ amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32
  *               of 2, 4 or 8 blocks of 512 threads instead of one block, the
  *               phases separated by cluster barriers (for launches over fewer
  *               grids than SMs; 16-bit local columns).
+ *   k = 31:     as 15 (2 entries in flight, L2 prefetch 2 ahead) in blocks
+ *               of 1024 threads, two per SM, each split into teams of whole
+ *               warps on their own named barriers; setup sizes every team
+ *               by its grids' work so that all teams finish together (one
+ *               grid per team while there are at most two grids per block,
+ *               else two teams of 16 warps per block with lists of grids;
+ *               16-bit local columns).
  * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
-#define AMGDD_FAC_CANDIDATES 31
+#define AMGDD_FAC_CANDIDATES 32
 /* amgdd_autotune flags: also time candidates 18 and 19 (reordered row sums) */
 #define AMGDD_TUNE_ALLOW_REORDERED 1
 

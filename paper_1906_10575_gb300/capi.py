@@ -67,7 +67,7 @@ EXPORTS = [
     "amgdd_set_fac_kernel", "amgdd_autotune",
 ]
 
-FAC_CANDIDATES = 31
+FAC_CANDIDATES = 32
 TUNE_ALLOW_REORDERED = 1
 
 _lib = None

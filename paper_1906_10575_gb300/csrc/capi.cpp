@@ -398,6 +398,96 @@ cudaError_t settle(amgdd_handle h, DevGrow &g, cudaStream_t st, void **out)
 
 }  // namespace
 
+// Team plan of the team-partitioned FAC kernel over nblocks blocks of 32
+// warps (at most 15 teams per block). Up to two grids per block on average:
+// one grid per team, its warps in proportion to its work. The smallest
+// per-warp work T for which every grid's ceil(work / T) warps (2 to 32)
+// pack into the blocks, first fit by decreasing need, is found by bisection;
+// each block's warps left over then go one at a time to its team with the
+// most work per warp. More grids: two teams of 16 warps per block, each grid
+// (largest first) to the team with the least work so far.
+struct TeamPlan {
+    std::vector<int32_t> block_off, w0, nw, grid_off, grid;
+};
+
+static TeamPlan plan_teams(const std::vector<int64_t> &work_in, int nblocks)
+{
+    const int nsub = (int)work_in.size();
+    std::vector<double> w((size_t)nsub);
+    for (int g = 0; g < nsub; ++g) w[g] = (double)std::max<int64_t>(work_in[g], 1);
+    std::vector<int32_t> ord((size_t)nsub);
+    for (int g = 0; g < nsub; ++g) ord[g] = g;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return w[a] > w[b]; });
+    // per block: its teams as (grids, warps)
+    std::vector<std::vector<std::pair<std::vector<int32_t>, int>>> blk((size_t)nblocks);
+    if (nsub <= 2 * nblocks) {
+        auto pack = [&](double T, bool keep) {
+            std::vector<int> used((size_t)nblocks, 0), cnt((size_t)nblocks, 0);
+            if (keep)
+                for (auto &b : blk) b.clear();
+            for (int32_t g : ord) {   // decreasing work = decreasing need
+                const int need = (int)std::min(32.0, std::max(2.0, std::ceil(w[g] / T)));
+                int b = 0;
+                while (b < nblocks && (used[b] + need > 32 || cnt[b] >= 15)) ++b;
+                if (b == nblocks) return false;
+                used[b] += need;
+                ++cnt[b];
+                if (keep) blk[b].push_back({{g}, need});
+            }
+            return true;
+        };
+        double W = 0.0;
+        for (double x : w) W += x;
+        double lo = W / (32.0 * nblocks), hi = std::max(w[ord[0]], lo) * 2.0;
+        while (!pack(hi, false)) hi *= 2.0;
+        for (int it = 0; it < 60; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (pack(mid, false)) hi = mid;
+            else lo = mid;
+        }
+        pack(hi, true);
+        for (auto &b : blk) {
+            int used = 0;
+            for (auto &t : b) used += t.second;
+            while (used < 32 && !b.empty()) {
+                size_t best = 0;
+                for (size_t k = 1; k < b.size(); ++k)
+                    if (w[b[k].first[0]] / b[k].second > w[b[best].first[0]] / b[best].second) best = k;
+                ++b[best].second;
+                ++used;
+            }
+        }
+    } else {
+        std::vector<double> load((size_t)2 * nblocks, 0.0);
+        for (int b = 0; b < nblocks; ++b) {
+            blk[b].push_back({{}, 16});
+            blk[b].push_back({{}, 16});
+        }
+        for (int32_t g : ord) {
+            size_t best = 0;
+            for (size_t k = 1; k < load.size(); ++k)
+                if (load[k] < load[best]) best = k;
+            blk[best / 2][best % 2].first.push_back(g);
+            load[best] += w[g];
+        }
+    }
+    TeamPlan T;
+    T.block_off.push_back(0);
+    T.grid_off.push_back(0);
+    for (auto &b : blk) {
+        int w0 = 0;
+        for (auto &t : b) {
+            T.w0.push_back(w0);
+            T.nw.push_back(t.second);
+            w0 += t.second;
+            T.grid.insert(T.grid.end(), t.first.begin(), t.first.end());
+            T.grid_off.push_back((int32_t)T.grid.size());
+        }
+        T.block_off.push_back((int32_t)T.w0.size());
+    }
+    return T;
+}
+
 // Fills the FAC kernel parameters of one composite-grid layout (all grids,
 // all levels of its hierarchy): the views, map and l1 weights already streamed
 // to the device by S, the small per-grid tables, the per-SM bins and the
@@ -503,6 +593,39 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, FacStream &S, int nl
         P.bin_off = doff;
         P.bin_grid = dgrid;
         P.ctr = dctr;
+        // teams for two blocks of 1024 threads per SM; the kernel's named
+        // barriers allow at most 15 teams per block (ids 1..15), each of
+        // 1..32 whole warps within the block's 32, and every grid must be
+        // cycled exactly once
+        const TeamPlan TP = plan_teams(F.work, 2 * nb);
+        {
+            bool ok = (int)TP.block_off.size() == 2 * nb + 1 && TP.grid_off.size() == TP.w0.size() + 1 &&
+                      (int)TP.grid.size() == nsub;
+            for (int b = 0; ok && b < 2 * nb; ++b) {
+                const int k0 = TP.block_off[b], k1 = TP.block_off[b + 1];
+                ok = k1 - k0 <= 15;
+                for (int k = k0; ok && k < k1; ++k)
+                    ok = TP.nw[k] >= 1 && TP.w0[k] >= 0 && TP.w0[k] + TP.nw[k] <= 32 &&
+                         (k == k0 || TP.w0[k] >= TP.w0[k - 1] + TP.nw[k - 1]);
+            }
+            std::vector<char> seen((size_t)nsub, 0);
+            for (int32_t g : TP.grid) {
+                ok = ok && g >= 0 && g < nsub && !seen[g];
+                if (ok) seen[g] = 1;
+            }
+            if (!ok) {
+                *what = "team plan of the FAC kernel";
+                return cudaErrorInvalidValue;
+            }
+        }
+        int32_t *tb, *tw0, *tnw, *tgo, *tg;
+        UP(TP.block_off, &tb, "upload teams");
+        UP(TP.w0, &tw0, "upload teams");
+        UP(TP.nw, &tnw, "upload teams");
+        UP(TP.grid_off, &tgo, "upload teams");
+        UP(TP.grid, &tg, "upload teams");
+        if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return e;
+        P.teams = FacTeams{2 * nb, tb, tw0, tnw, tgo, tg};
     }
     P.max_grid_rows = 0;
     for (int p = 0; p < nsub; ++p) {
@@ -959,15 +1082,69 @@ static amgdd_status residual_norm(amgdd_handle h, const double *b, const double 
     return AMGDD_OK;
 }
 
+// Levels whose restriction has at most this many rows are restricted by one
+// block (k_chain) instead of one grid-wide launch each; a fine level of at
+// most this many rows also has its residual computed by that block.
+static constexpr int64_t kChainRows = 4096;
+
+// First level l whose restriction R_l and all coarser ones have at most
+// kChainRows rows (n_{l+1} <= kChainRows); the number of levels - 1 if none.
+static int chain_first(amgdd_handle h)
+{
+    const int nlev = (int)h->lev.size();
+    int lt = nlev - 1;
+    while (lt > 0 && h->lev[lt].n <= kChainRows) --lt;
+    return lt;
+}
+
+// r_{l+1} = R_l r_l for l = l0 .. L-1 as chain steps.
+static void chain_steps(amgdd_handle h, double *r_all, int l0, ChainParams &C)
+{
+    const int nlev = (int)h->lev.size();
+    C.nsteps = 0;
+    for (int l = l0; l + 1 < nlev; ++l)
+        C.step[C.nsteps++] = ChainStep{h->lev[l].R, r_all + h->level_off[l], r_all + h->level_off[l + 1]};
+}
+
 static amgdd_status restrict_all(amgdd_handle h, double *r_all, cudaStream_t st)
 {
     const int nlev = (int)h->lev.size();
-    for (int l = 0; l + 1 < nlev; ++l) {
+    const int lt = chain_first(h);
+    for (int l = 0; l < lt; ++l) {
         const DevLevel &D = h->lev[l];
         CK(launch_spmv(D.R, 0, D.R.rows, r_all + h->level_off[l], r_all + h->level_off[l + 1], 0, st),
            "restriction kernel");
         h->launches += 1;
     }
+    if (lt + 1 < nlev) {
+        ChainParams C{};
+        chain_steps(h, r_all, lt, C);
+        CK(launch_chain(C, st), "restriction chain kernel");
+        h->launches += 1;
+    }
+    return AMGDD_OK;
+}
+
+// The right-hand sides of an AMG-DD iteration: r = b - A x (its squared
+// norm in h->scal[0]) and r_l = R_{l-1} r_{l-1} on every level, into r_all.
+// A fine level of at most kChainRows rows does all of it in one block.
+static amgdd_status residual_restrict(amgdd_handle h, const double *b, const double *x, cudaStream_t st)
+{
+    if (h->lev[0].n > kChainRows) {
+        CK(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, st), "residual kernel");
+        h->launches += 2;
+        return restrict_all(h, h->r_all, st);
+    }
+    ChainParams C{};
+    C.residual = 1;
+    C.A = h->lev[0].A;
+    C.b = b;
+    C.x = x;
+    C.r = h->r_all;
+    C.nrm2 = h->scal;
+    chain_steps(h, h->r_all, 0, C);
+    CK(launch_chain(C, st), "residual and restriction chain kernel");
+    h->launches += 1;
     return AMGDD_OK;
 }
 
@@ -981,6 +1158,7 @@ static cudaError_t launch_candidate(amgdd_handle h, FacParams P, int nrhs, int k
         return launch_fac_all_grids(P, P.nsub, h->threads, st);
     }
     if (k < 18) return launch_fac_multi(P, P.nsub, nrhs, k - 8, st);
+    if (k == 31) return launch_fac_multi(P, P.nsub, nrhs, 16, st);      // teams sized by work
     if (k >= 25) {   // one queue, largest grid first
         P.nbins = 1;
         P.bin_off = h->one_bin_off;
@@ -1159,8 +1337,7 @@ amgdd_status amgdd_iterate(amgdd_handle h, const double *b, double *x, void *str
     if (!b || !x) return fail(h, AMGDD_ERR_INVALID_ARG, "null vector");
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
-    if ((s = residual_norm(h, b, x, h->r_all, st, nullptr)) != AMGDD_OK) return s;
-    if ((s = restrict_all(h, h->r_all, st)) != AMGDD_OK) return s;
+    if ((s = residual_restrict(h, b, x, st)) != AMGDD_OK) return s;
     return fac(h, h->r_all, x, st);
 }
 
@@ -1189,14 +1366,19 @@ static amgdd_status capture_iteration(amgdd_handle h, int method, const double *
     cudaStream_t cs = h->cap_stream;
     const int64_t l0 = h->launches;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
-    amgdd_status s = amgdd ? restrict_all(h, h->r_all, cs)
+    // AMG-DD: the FAC launch on the right-hand sides left by the previous
+    // iteration (or by solve_loop), then the residual of the new iterate and
+    // its restriction for the next one
+    amgdd_status s = amgdd ? fac(h, h->r_all, x, cs)
                            : method == 1 ? vcycle(h, b, x, cs) : vcycle_hybrid(h, b, x, cs);
-    if (s == AMGDD_OK && amgdd) s = fac(h, h->r_all, x, cs);
-    if (s == AMGDD_OK) {
+    if (s == AMGDD_OK && amgdd) s = residual_restrict(h, b, x, cs);
+    if (s == AMGDD_OK && !amgdd) {
         cudaError_t e = launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, cs);
         h->launches += 2;
+        if (e != cudaSuccess) s = cuda_fail(h, e, "capture residual");
+    }
+    if (s == AMGDD_OK) {
+        cudaError_t e = cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, cs);
         if (e != cudaSuccess) s = cuda_fail(h, e, "capture residual");
     }
     cudaGraph_t graph = nullptr;
@@ -1228,7 +1410,14 @@ static amgdd_status solve_loop(amgdd_handle h, const double *b, double *x, doubl
     h->launches += 2;
     CK(cudaMemcpyAsync(h->h_scal + 1, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
     double nr2 = 0.0;
-    if ((s = residual_norm(h, b, x, h->r_all, st, &nr2)) != AMGDD_OK) return s;
+    if (method == 0) {
+        if ((s = residual_restrict(h, b, x, st)) != AMGDD_OK) return s;
+        CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
+        CK(cudaStreamSynchronize(st), "residual");
+        nr2 = h->h_scal[0];
+    } else if ((s = residual_norm(h, b, x, h->r_all, st, &nr2)) != AMGDD_OK) {
+        return s;
+    }
     double ref = std::sqrt(h->h_scal[1]);
     int32_t k = 0;
     double rel = 0.0;
@@ -1470,7 +1659,8 @@ amgdd_status amg_hybrid_solve(amgdd_handle h, const double *b, double *x, double
 // bins, 26 and 27 the kernel that keeps each grid's work vectors in shared
 // memory (two entries in flight and two blocks per SM, or four and one) on
 // that queue, 28-30 the kernel that cycles each grid with a cluster of 2, 4
-// or 8 blocks, on that queue.
+// or 8 blocks, on that queue, 31 variant 7 in work-sized teams of warps
+// (blocks of 1024 threads).
 static bool candidate_applies(amgdd_handle h, int nrhs, int k)
 {
     if (k < 0 || k >= AMGDD_FAC_CANDIDATES) return false;

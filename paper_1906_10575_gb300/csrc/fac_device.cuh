@@ -8,8 +8,17 @@
 namespace amgdd {
 namespace dev {
 
+// The threads that cycle one composite grid: a whole block (bar = 0), or a
+// team of whole warps inside a block that waits on its own named barrier
+// (bar = 1..15) and never on the other teams.
 struct Block {
     int lane, warp, nw, tid, nt;
+    int bar = 0;
+    __device__ __forceinline__ void sync() const
+    {
+        if (bar == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+    }
 };
 
 // Loads of operator entries, which every launch streams once: evict-first

@@ -51,16 +51,39 @@ __device__ __forceinline__ void prefetch_line(const void *p)
     else asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Where a pass reads a gathered level vector. One: local row c at x + c R.
+// Two: local row c at (c < split ? a : b) + c R, for a pass that reads the
+// rows below `split` from the buffer the previous half-sweep wrote them to
+// and the others from the buffer that still holds their current values.
+template <class T_, int R_>
+struct One {
+    using T = T_;
+    static constexpr int R = R_;
+    const T *x;
+    __device__ __forceinline__ const T *at(int64_t c) const { return x + c * R; }
+    __device__ __forceinline__ static One onchip(const T *p) { return One{p}; }
+};
+
+template <class T_, int R_>
+struct Two {
+    using T = T_;
+    static constexpr int R = R_;
+    const T *a, *b;
+    int split;
+    __device__ __forceinline__ const T *at(int64_t c) const { return (c < split ? a : b) + c * R; }
+    __device__ __forceinline__ static Two onchip(const T *p) { return Two{p, p, 0}; }
+};
+
 // s_j = sum_k a_k x[c_k * R + j] for the lane's row, one fma chain per column.
 // UNR entries are loaded before any of them is used (UNR operator loads and
 // UNR gathers in flight per lane); the fmas stay in ascending entry order.
 // PF != 0: each step first asks L2 (PF > 0) or L1 (PF < 0) for the operator
 // entries |PF| steps ahead, so their loads find them there instead of in HBM
 // (entries past the row's length are not touched).
-template <class CI, class T, int R, int UNR, int PF = 0, class SV>
-__device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint16_t *rlen, const CI *col,
+template <class CI, class T, int R, int UNR, int PF, class SV, class G>
+__device__ __forceinline__ VecR<T, R> sell_dot_g(const int64_t *soff, const uint16_t *rlen, const CI *col,
                                                  const SV *val, int64_t slice, int lane, int64_t row,
-                                                 const T *__restrict__ x)
+                                                 const G &x)
 {
     const int64_t base = __ldg(soff + slice) + lane;
     const int len = __ldg(rlen + row);
@@ -88,7 +111,7 @@ __device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint
 #pragma unroll
             for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<true>(val + base + 32 * (k + u));
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x + (int64_t)c[u] * R);
+            for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x.at(c[u]));
 #pragma unroll
             for (int u = 0; u < UNR; ++u)
 #pragma unroll
@@ -106,7 +129,7 @@ __device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint
 #pragma unroll
             for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<true>(val + base + 32 * (k + u));
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x + (int64_t)c[u] * R);
+            for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x.at(c[u]));
 #pragma unroll
             for (int u = 0; u < UNR; ++u)
 #pragma unroll
@@ -117,21 +140,30 @@ __device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint
     for (; k < len; ++k) {
         const int c = ld_op<true>(col + base + 32 * k);
         const T a = (T)ld_op<true>(val + base + 32 * k);
-        const VecR<T, R> xv = load_r<T, R>(x + (int64_t)c * R);
+        const VecR<T, R> xv = load_r<T, R>(x.at(c));
 #pragma unroll
         for (int j = 0; j < R; ++j) s.v[j] = fma(a, xv.v[j], s.v[j]);
     }
     return s;
 }
 
+// sell_dot_g over one plain vector x.
+template <class CI, class T, int R, int UNR, int PF = 0, class SV>
+__device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint16_t *rlen, const CI *col,
+                                                 const SV *val, int64_t slice, int lane, int64_t row,
+                                                 const T *__restrict__ x)
+{
+    return sell_dot_g<CI, T, R, UNR, PF, SV>(soff, rlen, col, val, slice, lane, row, One<T, R>{x});
+}
+
 // ---- composite grids ------------------------------------------------------
 
-template <class CI, class T, int R, int UNR, int PF>
+template <class CI, class T, int R, int UNR, int PF, class G>
 __device__ __forceinline__ VecR<T, R> view_dot_r(const FacViewDev &V, int64_t slice0, int64_t row0, int first,
-                                                 int r, const T *__restrict__ x)
+                                                 int r, const G &x)
 {
     const int v = r - first;
-    return sell_dot_r<CI, T, R, UNR, PF>(V.soff, V.rlen, static_cast<const CI *>(V.col), static_cast<const T *>(V.val),
+    return sell_dot_g<CI, T, R, UNR, PF, T>(V.soff, V.rlen, static_cast<const CI *>(V.col), static_cast<const T *>(V.val),
                                      slice0 + (v >> 5), v & 31, row0 + r, x);
 }
 
@@ -143,9 +175,9 @@ __device__ __forceinline__ VecR<T, R> view_dot_r(const FacViewDev &V, int64_t sl
 // an xor butterfly. The warp covers 32 / g consecutive rows of one slice per
 // pass, so rows of small levels spread over all warps and each lane's chain
 // is g times shorter; the rounding order is not the ascending chain's.
-template <class CI, class T, int R, int UNR, int PF, bool GRP, class Fn>
+template <class CI, class T, int R, int UNR, int PF, bool GRP, class G, class Fn>
 __device__ __forceinline__ void rows_dot(const Block &B, int g, const FacViewDev &V, int64_t s0, int64_t row0,
-                                         int first, int r0, int r1, const T *__restrict__ x, Fn &&fn)
+                                         int first, int r0, int r1, const G &x, Fn &&fn)
 {
     if (!GRP || g <= 1) {
         for_rows(B, first, r0, r1, [&](int r) { fn(r, view_dot_r<CI, T, R, UNR, PF>(V, s0, row0, first, r, x)); });
@@ -172,7 +204,7 @@ __device__ __forceinline__ void rows_dot(const Block &B, int g, const FacViewDev
             for (; k + g < len; k += 2 * g) {
                 const int c0 = ld_op<true>(col + base + 32 * k), c1 = ld_op<true>(col + base + 32 * (k + g));
                 const T a0 = ld_op<true>(val + base + 32 * k), a1 = ld_op<true>(val + base + 32 * (k + g));
-                const VecR<T, R> x0 = load_r<T, R>(x + (int64_t)c0 * R), x1 = load_r<T, R>(x + (int64_t)c1 * R);
+                const VecR<T, R> x0 = load_r<T, R>(x.at(c0)), x1 = load_r<T, R>(x.at(c1));
 #pragma unroll
                 for (int q = 0; q < R; ++q) acc.v[q] = fma(a0, x0.v[q], acc.v[q]);
 #pragma unroll
@@ -181,7 +213,7 @@ __device__ __forceinline__ void rows_dot(const Block &B, int g, const FacViewDev
             if (k < len) {
                 const int c0 = ld_op<true>(col + base + 32 * k);
                 const T a0 = ld_op<true>(val + base + 32 * k);
-                const VecR<T, R> x0 = load_r<T, R>(x + (int64_t)c0 * R);
+                const VecR<T, R> x0 = load_r<T, R>(x.at(c0));
 #pragma unroll
                 for (int q = 0; q < R; ++q) acc.v[q] = fma(a0, x0.v[q], acc.v[q]);
             }
@@ -193,69 +225,253 @@ __device__ __forceinline__ void rows_dot(const Block &B, int g, const FacViewDev
     }
 }
 
-// Shared-memory staging of a gathered vector: when the n values of the level
-// vector x fit the block's SB-byte buffer, the block copies them there and the
-// pass's gathers read the copy (the pass writes other vectors only, and the
-// previous pass ended at a barrier). Called by every thread of the block; the
-// condition is the same for all of them.
-template <int SB, class T>
-__device__ __forceinline__ const T *stage(const Block &B, const T *__restrict__ x, int64_t n, unsigned char *buf)
+// Shared-memory staging of a gathered vector: when the nrows rows of the
+// level vector x fit the block's SB-byte buffer, the block copies them there
+// and the pass's gathers read the copy (the pass writes other rows or other
+// vectors only, and the previous pass ended at a barrier). Called by every
+// thread of the block; the condition is the same for all of them.
+template <int SB, class G>
+__device__ __forceinline__ G stage(const Block &B, const G &x, int64_t nrows, unsigned char *buf)
 {
+    using T = typename G::T;
+    constexpr int R = G::R;
     if constexpr (SB > 0) {
-        if (n * (int64_t)sizeof(T) <= SB) {
+        if (nrows * R * (int64_t)sizeof(T) <= SB) {
             T *sb = reinterpret_cast<T *>(buf);
-            for (int64_t i = B.tid; i < n; i += B.nt) sb[i] = x[i];
-            __syncthreads();
-            return sb;
+            for (int64_t i = B.tid; i < nrows * R; i += B.nt) sb[i] = x.at(i / R)[i % R];
+            B.sync();
+            return G::onchip(sb);
         }
     }
     return x;
 }
 
-// One Jacobi half-sweep over rows [r0, r1): d = (f - V u) * (1/l1), then
-// u += d, t += d. in_place: no row of the pass reads u or t where another row
-// of the pass writes them (the F rows of the downsweep on l >= 1 read u at C
-// points only), so each row adds its own d at once: no scratch and no
-// barrier between the two steps, the same values.
-template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB>
+// One Jacobi half-sweep over the rows [r0, r1) of one set (C or F points):
+// v = (f - V u) * (1/l1) with u gathered through `src`; the row's new value
+// own + v goes to dst, and t becomes v (t_assign: t_l holds nothing of this
+// iteration yet) or t + v. dst is either the row's own buffer (in place:
+// the pass reads u only at rows outside the set) or the other buffer of the
+// pair, which the pass reads only outside the set; either way every read of
+// the pass sees the values from before it, as Jacobi needs, without a
+// scratch vector or a barrier between computing and applying.
+template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB, class G>
 __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B, const FacLevelDesc &d, int g,
                                              const FacViewDev &V, int64_t s0, int first, int r0, int r1,
-                                             unsigned char *buf, bool in_place = false)
+                                             const G &src, const T *own, T *dst, bool t_assign,
+                                             unsigned char *buf)
 {
-    T *__restrict__ u = static_cast<T *>(P.u) + d.row0 * R;
     T *__restrict__ t = static_cast<T *>(P.t) + d.row0 * R;
-    T *__restrict__ dd = static_cast<T *>(P.d) + d.row0 * R;
     const T *__restrict__ f = static_cast<const T *>(P.f) + d.row0 * R;
     const T *__restrict__ l1 = static_cast<const T *>(P.l1inv) + d.row0;
-    const T *ux = stage<SB>(B, u, (int64_t)d.nBar * R, buf);
-    if (in_place) {
-        rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, ux, [&](int r, const VecR<T, R> &s) {
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const T v = (f[r * R + j] - s.v[j]) * l1[r];
-                u[r * R + j] = u[r * R + j] + v;
-                t[r * R + j] = t[r * R + j] + v;
-            }
-        });
-        __syncthreads();
-        return;
-    }
-    rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, ux, [&](int r, const VecR<T, R> &s) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) dd[r * R + j] = (f[r * R + j] - s.v[j]) * l1[r];
-    });
-    __syncthreads();
-    for_rows(B, first, r0, r1, [&](int r) {
+    const G x = stage<SB>(B, src, (int64_t)d.nBar, buf);
+    rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, x, [&](int r, const VecR<T, R> &s) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            const T v = dd[r * R + j];
-            u[r * R + j] = u[r * R + j] + v;
-            t[r * R + j] = t[r * R + j] + v;
+            const T v = (f[r * R + j] - s.v[j]) * l1[r];
+            dst[r * R + j] = own[r * R + j] + v;
+            t[r * R + j] = t_assign ? v : t[r * R + j] + v;
         }
     });
-    __syncthreads();
+    B.sync();
 }
 
+// The composite-grid FAC launch (Algorithm 4 on every composite grid, the
+// owned corrections added to x as in Algorithm 2). u_l lives in two buffers,
+// U0 = P.u and U1 = P.d: a grid's level is either wholly in U0, or its real
+// rows are in U1 while its ghost rows stay in U0 (ghost rows are never
+// relaxed). Every level starts each AlgFAC cycle and ends the launch in U0:
+//   downsweep, l = 0: C half-sweep U0 -> U1, F half-sweep (C rows from U1)
+//     -> U1;
+//   downsweep, l >= 1: u_l = 0 with the first C half-sweep folded in, into
+//     U1 (ghosts: U0), then the in-place F half-sweep on U1;
+//   upsweep: u_l += P_l u_{l+1} (u_{l+1} in U0), then F half-sweep U1 -> U0
+//     (ghost columns from U0), C half-sweep (F and ghost columns from U0)
+//     U1 -> U0.
+// t_l is never cleared: the first write of each of its phases assigns, and
+// the s_l + A_l t_l product reads t only at real rows, which every half-sweep
+// pair writes. s_l + A_l t_l overwrites s_l, which nothing reads again
+// before the restriction from level l - 1 writes it in the next cycle (s_0
+// is zero in Algorithm 4, so on level 0 the product alone is stored).
+template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB>
+__device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, int p, unsigned char *fac_stage)
+{
+    T *__restrict__ U0 = static_cast<T *>(P.u);
+    T *__restrict__ U1 = static_cast<T *>(P.d);
+    T *__restrict__ Pf = static_cast<T *>(P.f);
+    T *__restrict__ Pt = static_cast<T *>(P.t);
+    T *__restrict__ Ps = static_cast<T *>(P.s);
+    const T *__restrict__ Pl1 = static_cast<const T *>(P.l1inv);
+    {
+        const FacLevelDesc *D = P.desc + (int64_t)p * P.nlev;
+        const int L = P.nlev - 1;
+
+        // f_l = r_l on the real rows of every level; u_0 = 0 (all its rows,
+        // in U0). Nothing else needs a start value: u_l (l >= 1) and s_l are
+        // written before they are read, t_l is assigned on first use.
+        for (int l = 0; l <= L; ++l) {
+            const FacLevelDesc d = D[l];
+            const double *__restrict__ rl = P.r_all + P.level_off[l] * R;
+            const int nr = l == 0 ? d.nBar : d.nReal;
+            for (int r = B.tid; r < nr; r += B.nt) {
+                const int64_t i = d.row0 + r;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    if (l == 0) U0[i * R + j] = T(0);
+                    if (r < d.nReal) Pf[i * R + j] = (T)rl[P.gmap[i] * R + j];
+                }
+            }
+        }
+        B.sync();
+
+        for (int c = 1; c <= P.nfac; ++c) {
+            const bool first_cycle = c == 1;
+            for (int l = 0; l < L; ++l) {
+                const FacLevelDesc d = D[l];
+                const FacLevelDesc dn = D[l + 1];
+                const int gl = GRP ? P.grp[l] : 1, gn = GRP ? P.grp[l + 1] : 1;
+                T *__restrict__ u0 = U0 + d.row0 * R;
+                T *__restrict__ u1 = U1 + d.row0 * R;
+                if (l > 0) {
+                    T *__restrict__ t = Pt + d.row0 * R;
+                    const T *__restrict__ f = Pf + d.row0 * R;
+                    const T *__restrict__ l1 = Pl1 + d.row0;
+                    for (int r = B.tid; r < d.nBar; r += B.nt) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            if (r < d.nC) {
+                                const T v = f[r * R + j] * l1[r];
+                                u1[r * R + j] = T(0) + v;
+                                t[r * R + j] = first_cycle ? v : t[r * R + j] + v;
+                            } else if (r < d.nReal) {
+                                u1[r * R + j] = T(0);
+                            } else {
+                                u0[r * R + j] = T(0);
+                            }
+                        }
+                    }
+                    B.sync();
+                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal,
+                                                             One<T, R>{u1}, u1, u1, first_cycle, fac_stage);
+                } else {
+                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC, One<T, R>{u0},
+                                                             u0, u1, first_cycle, fac_stage);
+                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal,
+                                                             Two<T, R>{u1, u0, d.nC}, u0, u1, first_cycle,
+                                                             fac_stage);
+                }
+                {
+                    // s_l <- s_l + A_l t_l (s_0 = 0)
+                    T *__restrict__ s = Ps + d.row0 * R;
+                    const One<T, R> t = stage<SB>(B, One<T, R>{Pt + d.row0 * R}, (int64_t)d.nBar, fac_stage);
+                    rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.At, d.sAt, d.row0, 0, 0, d.nBar, t,
+                                                     [&](int r, const VecR<T, R> &at) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j) s[r * R + j] = l == 0 ? at.v[j] : s[r * R + j] + at.v[j];
+                    });
+                }
+                B.sync();
+                {
+                    const One<T, R> w = stage<SB>(B, One<T, R>{Ps + d.row0 * R}, (int64_t)d.nBar, fac_stage);
+                    const One<T, R> un{U0 + dn.row0 * R};
+                    T *__restrict__ s1 = Ps + dn.row0 * R;
+                    T *__restrict__ f1 = Pf + dn.row0 * R;
+                    // s_{l+1} = R_l w_l on every row of level l+1; then, on its
+                    // real rows, f_{l+1} -= A_{l+1} u_{l+1} (cycles after the
+                    // first; u_{l+1} is in U0 from the previous upsweep) and
+                    // f_{l+1} -= s_{l+1}
+                    if (!GRP || gn <= 1) {
+                        for_rows(B, 0, 0, dn.nBar, [&](int r) {
+                            const VecR<T, R> sv = view_dot_r<CI, T, R, UNR, PF>(P.R, dn.sR, dn.row0, 0, r, w);
+#pragma unroll
+                            for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
+                            if (r < dn.nReal) {
+                                if (!first_cycle) {
+                                    const VecR<T, R> au =
+                                        view_dot_r<CI, T, R, UNR, PF>(P.A, dn.sA, dn.row0, 0, r, un);
+#pragma unroll
+                                    for (int j = 0; j < R; ++j)
+                                        f1[r * R + j] = (f1[r * R + j] - au.v[j]) - sv.v[j];
+                                } else {
+#pragma unroll
+                                    for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
+                                }
+                            }
+                        });
+                    } else {
+                        // groups: two traversals; row r has the same owning
+                        // lane in both, which reads back its own s_{l+1}
+                        rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.R, dn.sR, dn.row0, 0, 0, dn.nBar, w,
+                                                         [&](int r, const VecR<T, R> &sv) {
+#pragma unroll
+                            for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
+                            if (first_cycle && r < dn.nReal) {
+#pragma unroll
+                                for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
+                            }
+                        });
+                        if (!first_cycle)
+                            rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.A, dn.sA, dn.row0, 0, 0, dn.nReal, un,
+                                                             [&](int r, const VecR<T, R> &au) {
+#pragma unroll
+                                for (int j = 0; j < R; ++j)
+                                    f1[r * R + j] = (f1[r * R + j] - au.v[j]) - s1[r * R + j];
+                            });
+                    }
+                }
+                B.sync();
+            }
+            {
+                const FacLevelDesc d = D[L];
+                const T *__restrict__ f = Pf + d.row0 * R;
+                T *__restrict__ u = U0 + d.row0 * R;
+                // u_L = A_L^{-1} f_L in FP64 over the nonzeros of the inverse:
+                // the chain starts at +0 and never returns to -0, so each
+                // skipped fma(0, f_J, s) would have left s unchanged (finite f)
+                for (int e = B.tid; e < P.nL * R; e += B.nt) {
+                    const int I = e / R, j = e % R;
+                    double s = 0.0;
+                    const int32_t k1 = __ldg(P.ainv_ptr + I + 1);
+                    for (int32_t k = __ldg(P.ainv_ptr + I); k < k1; ++k)
+                        s = fma(__ldg(P.ainv_val + k), (double)f[__ldg(P.ainv_col + k) * R + j], s);
+                    u[I * R + j] = (T)s;
+                }
+            }
+            B.sync();
+            for (int l = L - 1; l >= 0; --l) {
+                const FacLevelDesc d = D[l];
+                const FacLevelDesc dn = D[l + 1];
+                T *__restrict__ u0 = U0 + d.row0 * R;
+                T *__restrict__ u1 = U1 + d.row0 * R;
+                const One<T, R> un = stage<SB>(B, One<T, R>{U0 + dn.row0 * R}, (int64_t)dn.nBar, fac_stage);
+                const int gl = GRP ? P.grp[l] : 1;
+                // u_l += P_l u_{l+1}: real rows in U1, ghost rows in U0
+                rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.P, d.sP, d.row0, 0, 0, d.nBar, un,
+                                                 [&](int r, const VecR<T, R> &pu) {
+                    T *u = r < d.nReal ? u1 : u0;
+#pragma unroll
+                    for (int j = 0; j < R; ++j) u[r * R + j] = u[r * R + j] + pu.v[j];
+                });
+                B.sync();
+                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal,
+                                                         Two<T, R>{u1, u0, d.nReal}, u1, u0, true, fac_stage);
+                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC,
+                                                         Two<T, R>{u1, u0, d.nC}, u1, u0, true, fac_stage);
+            }
+        }
+
+        const FacLevelDesc d0 = D[0];
+        const int64_t o0 = P.owned0[p], o1 = P.owned0[p + 1];
+        for (int64_t k = o0 + B.tid; k < o1; k += B.nt) {
+            const int64_t i = d0.row0 + P.owned[k];
+            const int64_t g = P.gmap[i];
+#pragma unroll
+            for (int j = 0; j < R; ++j) P.x[g * R + j] = P.x[g * R + j] + (double)U0[i * R + j];
+        }
+    }
+}
+
+// One block of 512 threads per composite grid at a time; a block claims its
+// grids from the bin of the SM it runs on, then from the other bins.
 template <class CI, class T, int R, int UNR, int MINB, int PF, bool GRP, int SB>
 __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
 {
@@ -266,12 +482,6 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
     B.lane = threadIdx.x & 31;
     B.warp = threadIdx.x >> 5;
     B.nw = blockDim.x >> 5;
-    T *__restrict__ Pu = static_cast<T *>(P.u);
-    T *__restrict__ Pf = static_cast<T *>(P.f);
-    T *__restrict__ Pt = static_cast<T *>(P.t);
-    T *__restrict__ Ps = static_cast<T *>(P.s);
-    T *__restrict__ Pw = static_cast<T *>(P.w);
-    const T *__restrict__ Pl1 = static_cast<const T *>(P.l1inv);
     __shared__ int claimed;
     for (;;) {
         __syncthreads();
@@ -289,168 +499,32 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
         __syncthreads();
         const int p = claimed;
         if (p < 0) break;
-        const FacLevelDesc *D = P.desc + (int64_t)p * P.nlev;
-        const int L = P.nlev - 1;
-
-        for (int l = 0; l <= L; ++l) {
-            const FacLevelDesc d = D[l];
-            const double *__restrict__ rl = P.r_all + P.level_off[l] * R;
-            for (int r = B.tid; r < d.nBar; r += B.nt) {
-                const int64_t i = d.row0 + r;
-                const int64_t g = P.gmap[i];
-                // t accumulates from zero on every level; u_0 and s_0 start at
-                // zero and nothing else writes s_0; u_l and s_l (l >= 1) are
-                // written before they are read (the downsweep initialises u_l,
-                // the restriction from level l-1 writes s_l)
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    Pt[i * R + j] = T(0);
-                    if (l == 0) {
-                        Pu[i * R + j] = T(0);
-                        Ps[i * R + j] = T(0);
-                    }
-                    if (r < d.nReal) Pf[i * R + j] = (T)rl[g * R + j];
-                }
-            }
-        }
-        __syncthreads();
-
-        for (int c = 1; c <= P.nfac; ++c) {
-            for (int l = 0; l < L; ++l) {
-                const FacLevelDesc d = D[l];
-                const FacLevelDesc dn = D[l + 1];
-                const int gl = GRP ? P.grp[l] : 1, gn = GRP ? P.grp[l + 1] : 1;
-                if (l > 0) {
-                    T *__restrict__ u = Pu + d.row0 * R;
-                    T *__restrict__ t = Pt + d.row0 * R;
-                    const T *__restrict__ f = Pf + d.row0 * R;
-                    const T *__restrict__ l1 = Pl1 + d.row0;
-                    for (int r = B.tid; r < d.nBar; r += B.nt) {
-#pragma unroll
-                        for (int j = 0; j < R; ++j) {
-                            if (r < d.nC) {
-                                const T v = f[r * R + j] * l1[r];
-                                u[r * R + j] = T(0) + v;
-                                t[r * R + j] = t[r * R + j] + v;
-                            } else {
-                                u[r * R + j] = T(0);
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, fac_stage,
-                                                             true);
-                } else {
-                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC, fac_stage);
-                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal, fac_stage);
-                }
-                {
-                    const T *__restrict__ s = Ps + d.row0 * R;
-                    T *__restrict__ w = Pw + d.row0 * R;
-                    const T *t = stage<SB>(B, Pt + d.row0 * R, (int64_t)d.nBar * R, fac_stage);
-                    rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.At, d.sAt, d.row0, 0, 0, d.nBar, t,
-                                                     [&](int r, const VecR<T, R> &at) {
-#pragma unroll
-                        for (int j = 0; j < R; ++j) w[r * R + j] = s[r * R + j] + at.v[j];
-                    });
-                }
-                __syncthreads();
-                {
-                    const T *w = stage<SB>(B, Pw + d.row0 * R, (int64_t)d.nBar * R, fac_stage);
-                    T *__restrict__ s1 = Ps + dn.row0 * R;
-                    T *__restrict__ f1 = Pf + dn.row0 * R;
-                    const T *__restrict__ u1 = Pu + dn.row0 * R;
-                    // s_{l+1} = R_l w_l on every row of level l+1; then, on its
-                    // real rows, f_{l+1} -= A_{l+1} u_{l+1} (cycles after the
-                    // first) and f_{l+1} -= s_{l+1}
-                    if (!GRP || gn <= 1) {
-                        for_rows(B, 0, 0, dn.nBar, [&](int r) {
-                            const VecR<T, R> sv = view_dot_r<CI, T, R, UNR, PF>(P.R, dn.sR, dn.row0, 0, r, w);
-#pragma unroll
-                            for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
-                            if (r < dn.nReal) {
-                                if (c > 1) {
-                                    const VecR<T, R> au =
-                                        view_dot_r<CI, T, R, UNR, PF>(P.A, dn.sA, dn.row0, 0, r, u1);
-#pragma unroll
-                                    for (int j = 0; j < R; ++j)
-                                        f1[r * R + j] = (f1[r * R + j] - au.v[j]) - sv.v[j];
-                                } else {
-#pragma unroll
-                                    for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
-                                }
-                            }
-                        });
-                    } else {
-                        // groups: two traversals; row r has the same owning
-                        // lane in both, which reads back its own s_{l+1}
-                        rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.R, dn.sR, dn.row0, 0, 0, dn.nBar, w,
-                                                         [&](int r, const VecR<T, R> &sv) {
-#pragma unroll
-                            for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
-                            if (c == 1 && r < dn.nReal) {
-#pragma unroll
-                                for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
-                            }
-                        });
-                        if (c > 1)
-                            rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.A, dn.sA, dn.row0, 0, 0, dn.nReal, u1,
-                                                             [&](int r, const VecR<T, R> &au) {
-#pragma unroll
-                                for (int j = 0; j < R; ++j)
-                                    f1[r * R + j] = (f1[r * R + j] - au.v[j]) - s1[r * R + j];
-                            });
-                    }
-                    T *__restrict__ t = Pt + d.row0 * R;
-                    // reset t_l; s_l needs no reset (s_0 stays zero, the next
-                    // downsweep's restriction overwrites s_l for l >= 1)
-                    for (int r = B.tid; r < d.nBar * R; r += B.nt) t[r] = T(0);
-                }
-                __syncthreads();
-            }
-            {
-                const FacLevelDesc d = D[L];
-                const T *__restrict__ f = Pf + d.row0 * R;
-                T *__restrict__ u = Pu + d.row0 * R;
-                // u_L = A_L^{-1} f_L in FP64 over the nonzeros of the inverse:
-                // the chain starts at +0 and never returns to -0, so each
-                // skipped fma(0, f_J, s) would have left s unchanged (finite f)
-                for (int e = B.tid; e < P.nL * R; e += B.nt) {
-                    const int I = e / R, j = e % R;
-                    double s = 0.0;
-                    const int32_t k1 = __ldg(P.ainv_ptr + I + 1);
-                    for (int32_t k = __ldg(P.ainv_ptr + I); k < k1; ++k)
-                        s = fma(__ldg(P.ainv_val + k), (double)f[__ldg(P.ainv_col + k) * R + j], s);
-                    u[I * R + j] = (T)s;
-                }
-            }
-            __syncthreads();
-            for (int l = L - 1; l >= 0; --l) {
-                const FacLevelDesc d = D[l];
-                const FacLevelDesc dn = D[l + 1];
-                T *__restrict__ u = Pu + d.row0 * R;
-                const T *u1 = stage<SB>(B, Pu + dn.row0 * R, (int64_t)dn.nBar * R, fac_stage);
-                const int gl = GRP ? P.grp[l] : 1;
-                rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.P, d.sP, d.row0, 0, 0, d.nBar, u1,
-                                                 [&](int r, const VecR<T, R> &pu) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) u[r * R + j] = u[r * R + j] + pu.v[j];
-                });
-                __syncthreads();
-                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal, fac_stage);
-                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC, fac_stage);
-            }
-        }
-
-        const FacLevelDesc d0 = D[0];
-        const int64_t o0 = P.owned0[p], o1 = P.owned0[p + 1];
-        for (int64_t k = o0 + B.tid; k < o1; k += B.nt) {
-            const int64_t i = d0.row0 + P.owned[k];
-            const int64_t g = P.gmap[i];
-#pragma unroll
-            for (int j = 0; j < R; ++j) P.x[g * R + j] = P.x[g * R + j] + (double)Pu[i * R + j];
-        }
+        fac_grid_r<CI, T, R, UNR, PF, GRP, SB>(P, B, p, fac_stage);
     }
+}
+
+// Teams: blocks of 1024 threads (two per SM), each split by the host into up
+// to 15 teams of whole warps; team k of a block cycles the grids of its list
+// in order, waiting only on its own named barrier (k + 1). The host sizes each
+// team by the work of its grids, so that the teams of the whole launch finish
+// together instead of the largest grids' blocks ending it alone.
+template <class CI, class T, int R, int UNR, int PF>
+__global__ void __launch_bounds__(1024, 2) k_fac_teams(FacParams P, FacTeams TT)
+{
+    const int w = threadIdx.x >> 5;
+    const int k0 = TT.block_off[blockIdx.x], k1 = TT.block_off[blockIdx.x + 1];
+    int k = k0;
+    while (k < k1 && !(w >= TT.w0[k] && w < TT.w0[k] + TT.nw[k])) ++k;
+    if (k >= k1) return;   // a warp of no team
+    Block B;
+    B.lane = threadIdx.x & 31;
+    B.warp = w - TT.w0[k];
+    B.nw = TT.nw[k];
+    B.tid = (int)threadIdx.x - 32 * TT.w0[k];
+    B.nt = 32 * TT.nw[k];
+    B.bar = k - k0 + 1;
+    for (int j = TT.grid_off[k]; j < TT.grid_off[k + 1]; ++j)
+        fac_grid_r<CI, T, R, UNR, PF, false, 0>(P, B, TT.grid[j], nullptr);
 }
 
 }  // namespace dev
@@ -468,8 +542,11 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
 //  13-15: as 7, with gathered level vectors of up to 16, 32 or 44 KB staged
 //      in shared memory (with the block's static shared memory, the total
 //      stays within the 48 KB a launch gets without an opt-in attribute)
+//  16: UNR 2, PF 2 in the team-partitioned kernel (blocks of 1024 threads,
+//      two per SM, split into teams sized by their grids' work; the plan is
+//      P.teams)
 // 32-bit local columns (composite levels above 65,535 points) use variant 1.
-constexpr int kMultiVariants = 15;
+constexpr int kMultiVariants = 16;
 
 template <class CI, class T, int R, int UNR, int MINB, int PF = 0, bool GRP = false, int SB = 0>
 cudaError_t launch_fac_r_variant(const FacParams &P, int nsub, cudaStream_t st)
@@ -489,11 +566,21 @@ cudaError_t launch_fac_r_variant(const FacParams &P, int nsub, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <class CI, class T, int R>
+cudaError_t launch_fac_teams_variant(const FacParams &P, cudaStream_t st)
+{
+    const FacTeams &TT = P.teams;
+    if (TT.nblocks < 1 || !TT.block_off || !TT.w0 || !TT.nw || !TT.grid_off || !TT.grid) return cudaErrorInvalidValue;
+    dev::k_fac_teams<CI, T, R, 2, 2><<<TT.nblocks, 1024, 0, st>>>(P, TT);
+    return cudaGetLastError();
+}
+
 template <class T, int R>
 cudaError_t launch_fac_r_typed(const FacParams &P, int nsub, int variant, cudaStream_t st)
 {
     if (!P.col16) return launch_fac_r_variant<int32_t, T, R, 1, 2>(P, nsub, st);
     switch (variant) {
+    case 16: return launch_fac_teams_variant<uint16_t, T, R>(P, st);
     case 2: return launch_fac_r_variant<uint16_t, T, R, 2, 2>(P, nsub, st);
     case 3: return launch_fac_r_variant<uint16_t, T, R, 2, 3>(P, nsub, st);
     case 4: return launch_fac_r_variant<uint16_t, T, R, 4, 2>(P, nsub, st);

@@ -108,6 +108,78 @@ __global__ void k_finish_sum(const double *__restrict__ partial, int n, double *
     }
 }
 
+// sell_dot with the gathered vector read through L2 (ld.global.cg): the
+// single-block chain reads vectors that it wrote itself one step earlier.
+__device__ __forceinline__ double sell_dot_cg(const int64_t *__restrict__ soff, const uint16_t *__restrict__ rlen,
+                                              const int32_t *__restrict__ col, const double *__restrict__ val,
+                                              int64_t slice, int lane, int64_t row, const double *x)
+{
+    const int64_t base = __ldg(soff + slice) + lane;
+    const int len = __ldg(rlen + row);
+    double s = 0.0;
+    const int32_t *c = col + base;
+    const double *v = val + base;
+    int k = 0;
+#pragma unroll 1
+    for (; k + 4 <= len; k += 4) {
+        const int32_t c0 = __ldg(c + 32 * (k + 0)), c1 = __ldg(c + 32 * (k + 1));
+        const int32_t c2 = __ldg(c + 32 * (k + 2)), c3 = __ldg(c + 32 * (k + 3));
+        const double v0 = __ldg(v + 32 * (k + 0)), v1 = __ldg(v + 32 * (k + 1));
+        const double v2 = __ldg(v + 32 * (k + 2)), v3 = __ldg(v + 32 * (k + 3));
+        const double x0 = __ldcg(x + c0), x1 = __ldcg(x + c1), x2 = __ldcg(x + c2), x3 = __ldcg(x + c3);
+        s = fma(v0, x0, s);
+        s = fma(v1, x1, s);
+        s = fma(v2, x2, s);
+        s = fma(v3, x3, s);
+    }
+    for (; k < len; ++k) s = fma(__ldg(v + 32 * k), __ldcg(x + __ldg(c + 32 * k)), s);
+    return s;
+}
+
+// The work of ChainParams on one block of 1024 threads (32 warps, one SELL
+// slice per warp at a time).
+__global__ void __launch_bounds__(1024, 1) k_chain(ChainParams C)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (C.residual) {
+        const SellView &A = C.A;
+        const int64_t nslices = (A.rows + 31) / 32;
+        double acc = 0.0;
+        for (int64_t q = warp; q < nslices; q += nw) {
+            const int64_t row = q * 32 + lane;
+            if (row < A.rows) {
+                const int32_t i = A.rowid ? __ldg(A.rowid + row) : (int32_t)row;
+                const double s = sell_dot_cg(A.soff, A.rlen, A.col, A.val, q, lane, row, C.x);
+                const double ri = C.b[i] - s;
+                C.r[i] = ri;
+                acc = fma(ri, ri, acc);
+            }
+        }
+        __shared__ double red[32];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            double v = lane < nw ? red[lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) C.nrm2[0] = v;
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < C.nsteps; ++k) {
+        const ChainStep &S = C.step[k];
+        const int64_t nslices = (S.M.rows + 31) / 32;
+        for (int64_t q = warp; q < nslices; q += nw) {
+            const int64_t row = q * 32 + lane;
+            if (row < S.M.rows) {
+                const int32_t i = S.M.rowid ? __ldg(S.M.rowid + row) : (int32_t)row;
+                S.y[i] = sell_dot_cg(S.M.soff, S.M.rlen, S.M.col, S.M.val, q, lane, row, S.x);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // y[i] = M_i . x (mode 0) or y[i] = y[i] + M_i . x (mode 1) over rows [r0, r1).
 __global__ void k_spmv(SellView M, int64_t r0, int64_t r1, const double *__restrict__ x, double *__restrict__ y,
                        int mode)
@@ -517,6 +589,13 @@ cudaError_t launch_residual(const SellView &A, const double *b, const double *x,
 {
     dev::k_residual<<<nblocks, 256, 0, st>>>(A, b, x, r, partial);
     dev::k_finish_sum<<<1, 1024, 0, st>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain(const ChainParams &C, cudaStream_t st)
+{
+    if (!C.residual && C.nsteps <= 0) return cudaSuccess;
+    dev::k_chain<<<1, 1024, 0, st>>>(C);
     return cudaGetLastError();
 }
 

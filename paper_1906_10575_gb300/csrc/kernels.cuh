@@ -44,6 +44,15 @@ struct FacViewDev {
 
 constexpr int kMaxLevels = 40;
 
+// Teams of the team-partitioned FAC kernel (variant 16): block b of the
+// launch holds teams [block_off[b], block_off[b + 1]); team k is warps
+// [w0[k], w0[k] + nw[k]) of its block and cycles grids
+// grid[grid_off[k] .. grid_off[k + 1]) in order.
+struct FacTeams {
+    int nblocks;
+    const int32_t *block_off, *w0, *nw, *grid_off, *grid;
+};
+
 struct FacParams {
     int nlev, nsub, nfac, nL;
     int col16;                  // 1: local columns are uint16_t
@@ -81,10 +90,31 @@ struct FacParams {
     // variants that keep them on chip (0: none; set by their launcher)
     int64_t max_grid_rows;
     int64_t vsm_bytes;
+    FacTeams teams;
 };
 
 cudaError_t launch_residual(const SellView &A, const double *b, const double *x, double *r, double *partial,
                             int nblocks, double *out, cudaStream_t st);
+
+// One block's worth of small sparse products, run back to back by a single
+// block of 1024 threads with a block barrier between them (no launch and no
+// grid-wide wait per step): optionally r = b - A x with sum r_i^2 in *nrm2,
+// then y = M x for each step in order (step k may read what step k - 1
+// wrote). Each row keeps the ascending fma chain of the multi-block kernels.
+struct ChainStep {
+    SellView M;
+    const double *x;
+    double *y;
+};
+struct ChainParams {
+    int residual;               // 1: the residual comes first
+    SellView A;
+    const double *b, *x;
+    double *r, *nrm2;
+    int nsteps;
+    ChainStep step[kMaxLevels];
+};
+cudaError_t launch_chain(const ChainParams &C, cudaStream_t st);
 cudaError_t launch_sumsq(const double *v, int64_t n, double *partial, int nblocks, double *out, cudaStream_t st);
 cudaError_t launch_spmv(const SellView &M, int64_t r0, int64_t r1, const double *x, double *y, int mode,
                         cudaStream_t st);

@@ -69,8 +69,22 @@ struct amgdd_handle_s {
         const double *b = nullptr;
         double *x = nullptr;
         int64_t launches = 0;
-    } graph[3];
+    };
     cudaStream_t cap_stream = nullptr;
+    // a whole solve per method as one graph (iterations in a while node),
+    // keyed by its vectors, tolerance and iteration limit
+    struct SolveGraph {
+        cudaGraphExec_t exec = nullptr;
+        const double *b = nullptr;
+        double *x = nullptr;
+        double tol = 0.0;
+        int32_t max_iter = -1;
+        int64_t pre_launches = 0, body_launches = 0;
+    } solve_graph[3];
+    cudaStream_t cap_stream2 = nullptr;     // captures the while node's body
+    ConvState *conv = nullptr, *h_conv = nullptr;   // device / pinned
+    double *hist = nullptr, *h_hist = nullptr;      // device / pinned, hist_cap doubles
+    int64_t hist_cap = 0;
     // work space of the several-right-hand-side path, per width (2 or 4)
     struct Multi {
         int R = 0;
@@ -714,13 +728,17 @@ void amgdd_destroy(amgdd_handle h)
     if (!h) return;
     if (h->on_device) {
         cudaStreamSynchronize(h->last_stream);
-        for (auto &g : h->graph)
-            if (g.exec) cudaGraphExecDestroy(g.exec);
         for (auto &m : h->multi) {
             if (m.graph.exec) cudaGraphExecDestroy(m.graph.exec);
             if (m.h_scal) cudaFreeHost(m.h_scal);
         }
+        for (auto &g : h->solve_graph)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+        if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+        if (h->hist) cudaFree(h->hist);
+        if (h->h_hist) cudaFreeHost(h->h_hist);
+        if (h->h_conv) cudaFreeHost(h->h_conv);
         for (void *p : h->allocs) cudaFree(p);
         if (h->h_scal) cudaFreeHost(h->h_scal);
     }
@@ -1350,51 +1368,113 @@ amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream
     return vcycle(h, b, x, (cudaStream_t)stream);
 }
 
-// Captures one solver iteration (the AMG-DD or V-cycle update followed by
-// the residual of the new iterate and the copy of its squared norm into
-// pinned host memory) as a CUDA graph on a private stream.
-static amgdd_status capture_iteration(amgdd_handle h, int method, const double *b, double *x)
+// The whole solve of a method as one graph: |b|^2, the residual of x_0 (and,
+// for AMG-DD, its restriction to every level) and the first convergence
+// check, then a while node whose body is one iteration (Algorithm 2, or the
+// V-cycle, or the hybrid cycle) followed by the residual of the new iterate
+// and the check; the check sets the node's condition, so the iterations run
+// back to back on the device with no host round trip between them.
+static amgdd_status capture_solve(amgdd_handle h, int method, const double *b, double *x, double tol,
+                                  int32_t max_iter)
 {
-    const bool amgdd = method == 0;
-    auto &G = h->graph[method];
-    if (G.exec && G.b == b && G.x == x) return AMGDD_OK;
+    auto &G = h->solve_graph[method];
+    if (G.exec && G.b == b && G.x == x && G.tol == tol && G.max_iter == max_iter) return AMGDD_OK;
     if (G.exec) {
         cudaGraphExecDestroy(G.exec);
-        G.exec = nullptr;
+        G = amgdd_handle_s::SolveGraph();
+    }
+    if ((int64_t)max_iter + 1 > h->hist_cap) {
+        if (h->hist) cudaFree(h->hist);
+        if (h->h_hist) cudaFreeHost(h->h_hist);
+        h->hist = nullptr;
+        h->h_hist = nullptr;
+        h->hist_cap = 0;
+        const int64_t cap = std::max<int64_t>((int64_t)max_iter + 1, 256);
+        CK(dev_malloc((void **)&h->hist, sizeof(double) * (size_t)cap), "alloc solve history");
+        CK(cudaMallocHost((void **)&h->h_hist, sizeof(double) * (size_t)cap), "alloc solve history");
+        h->hist_cap = cap;
+    }
+    if (!h->conv) {
+        CK(alloc(h, 1, &h->conv), "alloc convergence state");
+        CK(cudaMallocHost((void **)&h->h_conv, sizeof(ConvState)), "alloc convergence state");
     }
     if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
-    cudaStream_t cs = h->cap_stream;
+    if (!h->cap_stream2) CK(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t cs = h->cap_stream, cs2 = h->cap_stream2;
+    const bool amgdd = method == 0;
     const int64_t l0 = h->launches;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
-    // AMG-DD: the FAC launch on the right-hand sides left by the previous
-    // iteration (or by solve_loop), then the residual of the new iterate and
-    // its restriction for the next one
-    amgdd_status s = amgdd ? fac(h, h->r_all, x, cs)
-                           : method == 1 ? vcycle(h, b, x, cs) : vcycle_hybrid(h, b, x, cs);
-    if (s == AMGDD_OK && amgdd) s = residual_restrict(h, b, x, cs);
-    if (s == AMGDD_OK && !amgdd) {
-        cudaError_t e = launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs);
-        h->launches += 2;
-        if (e != cudaSuccess) s = cuda_fail(h, e, "capture residual");
-    }
-    if (s == AMGDD_OK) {
-        cudaError_t e = cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, cs);
-        if (e != cudaSuccess) s = cuda_fail(h, e, "capture residual");
-    }
+    amgdd_status s = AMGDD_OK;
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaGraphConditionalHandle hc = 0;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    auto step = [&](cudaError_t r, const char *what) {
+        if (s == AMGDD_OK && r != cudaSuccess) s = cuda_fail(h, r, what);
+        return s == AMGDD_OK;
+    };
+    cudaStreamCaptureStatus cst;
+    if (step(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph), "capture info") &&
+        step(cudaGraphConditionalHandleCreate(&hc, graph, 0, 0), "conditional handle") &&
+        step(launch_sumsq(b, h->lev[0].n, h->partial, h->nred, h->scal + 1, cs), "norm kernel")) {
+        h->launches += 2;
+        if (amgdd) {
+            s = residual_restrict(h, b, x, cs);
+        } else {
+            step(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs), "residual kernel");
+            h->launches += 2;
+        }
+    }
+    if (step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 1, cs), "check kernel")) {
+        h->launches += 1;
+        G.pre_launches = h->launches - l0;
+    }
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphNode_t wnode = nullptr;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (step(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps), "capture info") &&
+        step(cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &cp), "while node") &&
+        step(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies),
+             "capture dependencies") &&
+        step(cudaStreamBeginCaptureToGraph(cs2, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal),
+             "begin body capture")) {
+        const int64_t l1 = h->launches;
+        s = amgdd ? fac(h, h->r_all, x, cs2) : method == 1 ? vcycle(h, b, x, cs2) : vcycle_hybrid(h, b, x, cs2);
+        if (s == AMGDD_OK && amgdd) s = residual_restrict(h, b, x, cs2);
+        if (s == AMGDD_OK && !amgdd) {
+            step(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs2), "residual kernel");
+            h->launches += 2;
+        }
+        if (step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 0, cs2), "check kernel"))
+            h->launches += 1;
+        G.body_launches = h->launches - l1;
+        cudaGraph_t body = nullptr;
+        const cudaError_t eb = cudaStreamEndCapture(cs2, &body);
+        step(eb, "end body capture");
+    }
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(cs, &out);
+    h->launches = l0;
     if (s != AMGDD_OK) {
-        if (graph) cudaGraphDestroy(graph);
+        if (out) cudaGraphDestroy(out);
         return s;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
-    e = cudaGraphInstantiate(&G.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    e = cudaGraphInstantiate(&G.exec, out, 0);
+    cudaGraphDestroy(out);
+    if (e != cudaSuccess) {
+        G = amgdd_handle_s::SolveGraph();
+        return cuda_fail(h, e, "graph instantiate");
+    }
     G.b = b;
     G.x = x;
-    G.launches = h->launches - l0;
-    h->launches = l0;
+    G.tol = tol;
+    G.max_iter = max_iter;
     return AMGDD_OK;
 }
 
@@ -1402,43 +1482,27 @@ static amgdd_status solve_loop(amgdd_handle h, const double *b, double *x, doubl
                                cudaStream_t st, amgdd_solve_info *info, int method)
 {
     const auto t0 = std::chrono::steady_clock::now();
-    const int64_t l0 = h->launches;
     amgdd_status s;
-    if ((s = capture_iteration(h, method, b, x)) != AMGDD_OK) return s;
-    const auto &G = h->graph[method];
-    CK(launch_sumsq(b, h->lev[0].n, h->partial, h->nred, h->scal + 1, st), "norm kernel");
-    h->launches += 2;
-    CK(cudaMemcpyAsync(h->h_scal + 1, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
-    double nr2 = 0.0;
-    if (method == 0) {
-        if ((s = residual_restrict(h, b, x, st)) != AMGDD_OK) return s;
-        CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
-        CK(cudaStreamSynchronize(st), "residual");
-        nr2 = h->h_scal[0];
-    } else if ((s = residual_norm(h, b, x, h->r_all, st, &nr2)) != AMGDD_OK) {
-        return s;
-    }
-    double ref = std::sqrt(h->h_scal[1]);
-    int32_t k = 0;
-    double rel = 0.0;
-    for (;;) {
-        const double nr = std::sqrt(nr2);
-        if (k == 0 && ref == 0.0) ref = nr;
-        rel = ref > 0.0 ? nr / ref : 0.0;
-        if (info && info->history) info->history[k] = rel;
-        if (rel <= tol || k >= max_iter) break;
-        CK(cudaGraphLaunch(G.exec, st), "graph launch");
-        CK(cudaStreamSynchronize(st), "iteration");
-        h->launches += G.launches;
-        nr2 = h->h_scal[0];
-        ++k;
-    }
+    if (max_iter < 0) return fail(h, AMGDD_ERR_INVALID_ARG, "max_iter < 0");
+    if ((s = capture_solve(h, method, b, x, tol, max_iter)) != AMGDD_OK) return s;
+    const auto &G = h->solve_graph[method];
+    CK(cudaGraphLaunch(G.exec, st), "graph launch");
+    CK(cudaMemcpyAsync(h->h_conv, h->conv, sizeof(ConvState), cudaMemcpyDeviceToHost, st), "iteration count copy");
+    CK(cudaStreamSynchronize(st), "solve");
+    const int32_t k = h->h_conv->k;
+    if (k < 0 || k > max_iter) return fail(h, AMGDD_ERR_CUDA, "iteration count out of range");
+    CK(cudaMemcpyAsync(h->h_hist, h->hist, sizeof(double) * ((size_t)k + 1), cudaMemcpyDeviceToHost, st),
+       "history copy");
+    CK(cudaStreamSynchronize(st), "history copy");
+    const double rel = h->h_hist[k];
+    h->launches += G.pre_launches + (int64_t)k * G.body_launches;
     if (info) {
+        if (info->history) std::copy(h->h_hist, h->h_hist + k + 1, info->history);
         info->iterations = k;
         info->converged = rel <= tol;
         info->final_relres = rel;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        info->kernel_launches = h->launches - l0;
+        info->kernel_launches = G.pre_launches + (int64_t)k * G.body_launches;
     }
     if (!(rel <= tol)) return fail(h, AMGDD_ERR_NO_CONVERGENCE, "max_iter reached before tol");
     return AMGDD_OK;
@@ -1673,10 +1737,10 @@ static bool candidate_reorders(int k) { return k == 18 || k == 19; }
 
 static void drop_graphs(amgdd_handle h)
 {
-    for (auto &g : h->graph)
+    for (auto &g : h->solve_graph)
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
-            g = amgdd_handle_s::Graph();
+            g = amgdd_handle_s::SolveGraph();
         }
     for (auto &m : h->multi)
         if (m.graph.exec) {

@@ -180,6 +180,22 @@ __global__ void __launch_bounds__(1024, 1) k_chain(ChainParams C)
     }
 }
 
+__global__ void k_converge(cudaGraphConditionalHandle hc, const double *nrm2, const double *ref2, ConvState *cs,
+                           double *hist, double tol, int32_t max_iter, int first)
+{
+    if (threadIdx.x != 0) return;
+    const double nr = sqrt(nrm2[0]);
+    int32_t k = first ? 0 : cs->k;
+    double ref = first ? sqrt(ref2[0]) : cs->ref;
+    if (first && ref == 0.0) ref = nr;
+    const double rel = ref > 0.0 ? nr / ref : 0.0;
+    hist[k] = rel;
+    const bool more = !(rel <= tol) && k < max_iter;
+    cs->k = more ? k + 1 : k;
+    cs->ref = ref;
+    cudaGraphSetConditional(hc, more ? 1u : 0u);
+}
+
 // y[i] = M_i . x (mode 0) or y[i] = y[i] + M_i . x (mode 1) over rows [r0, r1).
 __global__ void k_spmv(SellView M, int64_t r0, int64_t r1, const double *__restrict__ x, double *__restrict__ y,
                        int mode)
@@ -596,6 +612,13 @@ cudaError_t launch_chain(const ChainParams &C, cudaStream_t st)
 {
     if (!C.residual && C.nsteps <= 0) return cudaSuccess;
     dev::k_chain<<<1, 1024, 0, st>>>(C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_converge(cudaGraphConditionalHandle hc, const double *nrm2, const double *ref2, ConvState *cs,
+                            double *hist, double tol, int32_t max_iter, int first, cudaStream_t st)
+{
+    dev::k_converge<<<1, 32, 0, st>>>(hc, nrm2, ref2, cs, hist, tol, max_iter, first);
     return cudaGetLastError();
 }
 

@@ -115,6 +115,20 @@ struct ChainParams {
     ChainStep step[kMaxLevels];
 };
 cudaError_t launch_chain(const ChainParams &C, cudaStream_t st);
+
+// Convergence state of a solve that runs its iterations in a graph's while
+// node: k = iterations done, ref = the norm relative residuals divide by.
+struct ConvState {
+    int32_t k;
+    int32_t pad;
+    double ref;
+};
+// One thread: rel = sqrt(*nrm2) / ref (first: k = 0, ref = sqrt(*ref2), or
+// the residual norm itself when that is zero), hist[k] = rel, and the while
+// node's condition set to "rel > tol (or NaN) and k < max_iter", k advancing
+// by the iteration about to run.
+cudaError_t launch_converge(cudaGraphConditionalHandle hc, const double *nrm2, const double *ref2, ConvState *cs,
+                            double *hist, double tol, int32_t max_iter, int first, cudaStream_t st);
 cudaError_t launch_sumsq(const double *v, int64_t n, double *partial, int nblocks, double *out, cudaStream_t st);
 cudaError_t launch_spmv(const SellView &M, int64_t r0, int64_t r1, const double *x, double *y, int mode,
                         cudaStream_t st);

@@ -42,7 +42,11 @@ typedef enum {
     AMGDD_ERR_OOM = 4,                 /* host or device allocation failed */
     AMGDD_ERR_CUDA = 5,                /* a CUDA runtime call failed */
     AMGDD_ERR_NO_CONVERGENCE = 6,      /* max_iter reached before tol */
-    AMGDD_ERR_DEVICE_TIMEOUT = 7,      /* reserved: a bounded device wait expired */
+    AMGDD_ERR_DEVICE_TIMEOUT = 7,      /* never returned by this version: no kernel of the
+                                          library waits on another block (grids are claimed
+                                          with atomicAdd, teams wait only on their own named
+                                          barrier, clusters on the hardware cluster barrier);
+                                          kept so that the code stays stable */
     AMGDD_ERR_SINGULAR = 8,            /* coarsest matrix is singular */
     AMGDD_ERR_NOT_ON_DEVICE = 9        /* handle was set up with host_only = 1 */
 } amgdd_status;

@@ -80,7 +80,7 @@ struct Two {
 // PF != 0: each step first asks L2 (PF > 0) or L1 (PF < 0) for the operator
 // entries |PF| steps ahead, so their loads find them there instead of in HBM
 // (entries past the row's length are not touched).
-template <class CI, class T, int R, int UNR, int PF, class SV, class G>
+template <class CI, class T, int R, int UNR, int PF, class SV, bool STREAM = true, class G>
 __device__ __forceinline__ VecR<T, R> sell_dot_g(const int64_t *soff, const uint16_t *rlen, const CI *col,
                                                  const SV *val, int64_t slice, int lane, int64_t row,
                                                  const G &x)
@@ -107,9 +107,9 @@ __device__ __forceinline__ VecR<T, R> sell_dot_g(const int64_t *soff, const uint
             T a[UNR];
             VecR<T, R> xv[UNR];
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) c[u] = ld_op<true>(col + base + 32 * (k + u));
+            for (int u = 0; u < UNR; ++u) c[u] = ld_op<STREAM>(col + base + 32 * (k + u));
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<true>(val + base + 32 * (k + u));
+            for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<STREAM>(val + base + 32 * (k + u));
 #pragma unroll
             for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x.at(c[u]));
 #pragma unroll
@@ -125,9 +125,9 @@ __device__ __forceinline__ VecR<T, R> sell_dot_g(const int64_t *soff, const uint
             T a[UNR];
             VecR<T, R> xv[UNR];
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) c[u] = ld_op<true>(col + base + 32 * (k + u));
+            for (int u = 0; u < UNR; ++u) c[u] = ld_op<STREAM>(col + base + 32 * (k + u));
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<true>(val + base + 32 * (k + u));
+            for (int u = 0; u < UNR; ++u) a[u] = (T)ld_op<STREAM>(val + base + 32 * (k + u));
 #pragma unroll
             for (int u = 0; u < UNR; ++u) xv[u] = load_r<T, R>(x.at(c[u]));
 #pragma unroll
@@ -138,8 +138,8 @@ __device__ __forceinline__ VecR<T, R> sell_dot_g(const int64_t *soff, const uint
     }
 #pragma unroll 1
     for (; k < len; ++k) {
-        const int c = ld_op<true>(col + base + 32 * k);
-        const T a = (T)ld_op<true>(val + base + 32 * k);
+        const int c = ld_op<STREAM>(col + base + 32 * k);
+        const T a = (T)ld_op<STREAM>(val + base + 32 * k);
         const VecR<T, R> xv = load_r<T, R>(x.at(c));
 #pragma unroll
         for (int j = 0; j < R; ++j) s.v[j] = fma(a, xv.v[j], s.v[j]);
@@ -158,13 +158,14 @@ __device__ __forceinline__ VecR<T, R> sell_dot_r(const int64_t *soff, const uint
 
 // ---- composite grids ------------------------------------------------------
 
-template <class CI, class T, int R, int UNR, int PF, class G>
+template <class CI, class T, int R, int UNR, int PF, bool STREAM = true, class G>
 __device__ __forceinline__ VecR<T, R> view_dot_r(const FacViewDev &V, int64_t slice0, int64_t row0, int first,
                                                  int r, const G &x)
 {
     const int v = r - first;
-    return sell_dot_g<CI, T, R, UNR, PF, T>(V.soff, V.rlen, static_cast<const CI *>(V.col), static_cast<const T *>(V.val),
-                                     slice0 + (v >> 5), v & 31, row0 + r, x);
+    return sell_dot_g<CI, T, R, UNR, PF, T, STREAM>(V.soff, V.rlen, static_cast<const CI *>(V.col),
+                                                    static_cast<const T *>(V.val), slice0 + (v >> 5), v & 31,
+                                                    row0 + r, x);
 }
 
 // Row products V_r . x of local rows [r0, r1) of a view whose slices start at
@@ -175,12 +176,13 @@ __device__ __forceinline__ VecR<T, R> view_dot_r(const FacViewDev &V, int64_t sl
 // an xor butterfly. The warp covers 32 / g consecutive rows of one slice per
 // pass, so rows of small levels spread over all warps and each lane's chain
 // is g times shorter; the rounding order is not the ascending chain's.
-template <class CI, class T, int R, int UNR, int PF, bool GRP, class G, class Fn>
+template <class CI, class T, int R, int UNR, int PF, bool GRP, bool STREAM = true, class G, class Fn>
 __device__ __forceinline__ void rows_dot(const Block &B, int g, const FacViewDev &V, int64_t s0, int64_t row0,
                                          int first, int r0, int r1, const G &x, Fn &&fn)
 {
     if (!GRP || g <= 1) {
-        for_rows(B, first, r0, r1, [&](int r) { fn(r, view_dot_r<CI, T, R, UNR, PF>(V, s0, row0, first, r, x)); });
+        for_rows(B, first, r0, r1,
+                 [&](int r) { fn(r, view_dot_r<CI, T, R, UNR, PF, STREAM>(V, s0, row0, first, r, x)); });
         return;
     }
     if (r1 <= r0) return;
@@ -254,17 +256,28 @@ __device__ __forceinline__ G stage(const Block &B, const G &x, int64_t nrows, un
 // pair, which the pass reads only outside the set; either way every read of
 // the pass sees the values from before it, as Jacobi needs, without a
 // scratch vector or a barrier between computing and applying.
-template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB, class G>
-__device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B, const FacLevelDesc &d, int g,
-                                             const FacViewDev &V, int64_t s0, int first, int r0, int r1,
-                                             const G &src, const T *own, T *dst, bool t_assign,
-                                             unsigned char *buf)
+// The work vectors of the grid being cycled: u in two buffers (u, u2), f, t
+// and s, R values per row. Row i of the composite layout (row0 + local row)
+// is entry i - rb: rb = 0 where they are the global arrays, rb = the grid's
+// first row where they sit in the block's shared memory.
+template <class T>
+struct WorkVecs {
+    T *u, *u2, *f, *t, *s;
+    int64_t rb;
+};
+
+template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB, bool STREAM, class G>
+__device__ __forceinline__ void relax_pass_r(const FacParams &P, const WorkVecs<T> &W, const Block &B,
+                                             const FacLevelDesc &d, int g, const FacViewDev &V, int64_t s0,
+                                             int first, int r0, int r1, const G &src, const T *own, T *dst,
+                                             bool t_assign, unsigned char *buf)
 {
-    T *__restrict__ t = static_cast<T *>(P.t) + d.row0 * R;
-    const T *__restrict__ f = static_cast<const T *>(P.f) + d.row0 * R;
+    T *__restrict__ t = W.t + (d.row0 - W.rb) * R;
+    const T *__restrict__ f = W.f + (d.row0 - W.rb) * R;
     const T *__restrict__ l1 = static_cast<const T *>(P.l1inv) + d.row0;
     const G x = stage<SB>(B, src, (int64_t)d.nBar, buf);
-    rows_dot<CI, T, R, UNR, PF, GRP>(B, g, V, s0, d.row0, first, r0, r1, x, [&](int r, const VecR<T, R> &s) {
+    rows_dot<CI, T, R, UNR, PF, GRP, STREAM>(B, g, V, s0, d.row0, first, r0, r1, x,
+                                             [&](int r, const VecR<T, R> &s) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const T v = (f[r * R + j] - s.v[j]) * l1[r];
@@ -281,26 +294,37 @@ __device__ __forceinline__ void relax_pass_r(const FacParams &P, const Block &B,
 // rows are in U1 while its ghost rows stay in U0 (ghost rows are never
 // relaxed). Every level starts each AlgFAC cycle and ends the launch in U0:
 //   downsweep, l = 0: C half-sweep U0 -> U1, F half-sweep (C rows from U1)
-//     -> U1;
+//     -> U1 (first cycle: u_0 = 0, so the C half-sweep is f / l1 and the F
+//     half-sweep reads the C columns only);
 //   downsweep, l >= 1: u_l = 0 with the first C half-sweep folded in, into
-//     U1 (ghosts: U0), then the in-place F half-sweep on U1;
-//   upsweep: u_l += P_l u_{l+1} (u_{l+1} in U0), then F half-sweep U1 -> U0
-//     (ghost columns from U0), C half-sweep (F and ghost columns from U0)
-//     U1 -> U0.
+//     U1, done row by row by the restriction pass from level l - 1 as soon
+//     as a row's f_l is final, then the in-place F half-sweep on U1;
+//   upsweep: u_l += P_l u_{l+1} (u_{l+1} in U0; on the ghost rows of
+//     l >= 1, which are zero until then, 0 + P_l u_{l+1} into U0), then F
+//     half-sweep U1 -> U0 (ghost columns from U0), C half-sweep (F and ghost
+//     columns from U0) U1 -> U0.
 // t_l is never cleared: the first write of each of its phases assigns, and
 // the s_l + A_l t_l product reads t only at real rows, which every half-sweep
 // pair writes. s_l + A_l t_l overwrites s_l, which nothing reads again
 // before the restriction from level l - 1 writes it in the next cycle (s_0
 // is zero in Algorithm 4, so on level 0 the product alone is stored).
-template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB>
-__device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, int p, unsigned char *fac_stage)
+template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB, bool STREAM = true>
+__device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, int p, const WorkVecs<T> &W,
+                                           unsigned char *fac_stage)
 {
-    T *__restrict__ U0 = static_cast<T *>(P.u);
-    T *__restrict__ U1 = static_cast<T *>(P.d);
-    T *__restrict__ Pf = static_cast<T *>(P.f);
-    T *__restrict__ Pt = static_cast<T *>(P.t);
-    T *__restrict__ Ps = static_cast<T *>(P.s);
+    T *__restrict__ U0 = W.u;
+    T *__restrict__ U1 = W.u2;
+    T *__restrict__ Pf = W.f;
+    T *__restrict__ Pt = W.t;
+    T *__restrict__ Ps = W.s;
+    const int64_t rb = W.rb;
     const T *__restrict__ Pl1 = static_cast<const T *>(P.l1inv);
+    // one half-sweep of level d over rows [r0, r1) of view V (slices from `first`)
+    auto relax = [&](const FacLevelDesc &d, int g, const FacViewDev &V, int64_t s0, int first, int r0, int r1,
+                     const auto &src, const T *own, T *dst, bool t_assign) {
+        relax_pass_r<CI, T, R, UNR, PF, GRP, SB, STREAM>(P, W, B, d, g, V, s0, first, r0, r1, src, own, dst, t_assign,
+                                                         fac_stage);
+    };
     {
         const FacLevelDesc *D = P.desc + (int64_t)p * P.nlev;
         const int L = P.nlev - 1;
@@ -316,8 +340,8 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
                 const int64_t i = d.row0 + r;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    if (l == 0) U0[i * R + j] = T(0);
-                    if (r < d.nReal) Pf[i * R + j] = (T)rl[P.gmap[i] * R + j];
+                    if (l == 0) U0[(i - rb) * R + j] = T(0);
+                    if (r < d.nReal) Pf[(i - rb) * R + j] = (T)rl[P.gmap[i] * R + j];
                 }
             }
         }
@@ -329,41 +353,39 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
                 const FacLevelDesc d = D[l];
                 const FacLevelDesc dn = D[l + 1];
                 const int gl = GRP ? P.grp[l] : 1, gn = GRP ? P.grp[l + 1] : 1;
-                T *__restrict__ u0 = U0 + d.row0 * R;
-                T *__restrict__ u1 = U1 + d.row0 * R;
+                T *__restrict__ u0 = U0 + (d.row0 - rb) * R;
+                T *__restrict__ u1 = U1 + (d.row0 - rb) * R;
                 if (l > 0) {
-                    T *__restrict__ t = Pt + d.row0 * R;
-                    const T *__restrict__ f = Pf + d.row0 * R;
+                    // u_l = 0 and its first C half-sweep were done row by row
+                    // by the restriction pass from level l - 1 (below)
+                    relax(d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, One<T, R>{u1}, u1, u1, first_cycle);
+                } else if (first_cycle) {
+                    // u_0 = 0 (prologue): every product of the C half-sweep is
+                    // +0, so its correction is f / l1 with no row product, and
+                    // the F half-sweep sees nonzero u only at C columns (view
+                    // AFc; the omitted products are exact zeros)
+                    T *__restrict__ t = Pt + (d.row0 - rb) * R;
+                    const T *__restrict__ f = Pf + (d.row0 - rb) * R;
                     const T *__restrict__ l1 = Pl1 + d.row0;
-                    for (int r = B.tid; r < d.nBar; r += B.nt) {
+                    for (int r = B.tid; r < d.nC; r += B.nt) {
 #pragma unroll
                         for (int j = 0; j < R; ++j) {
-                            if (r < d.nC) {
-                                const T v = f[r * R + j] * l1[r];
-                                u1[r * R + j] = T(0) + v;
-                                t[r * R + j] = first_cycle ? v : t[r * R + j] + v;
-                            } else if (r < d.nReal) {
-                                u1[r * R + j] = T(0);
-                            } else {
-                                u0[r * R + j] = T(0);
-                            }
+                            const T v = f[r * R + j] * l1[r];
+                            u1[r * R + j] = T(0) + v;
+                            t[r * R + j] = v;
                         }
                     }
                     B.sync();
-                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal,
-                                                             One<T, R>{u1}, u1, u1, first_cycle, fac_stage);
+                    relax(d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, One<T, R>{u1}, u0, u1, true);
                 } else {
-                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC, One<T, R>{u0},
-                                                             u0, u1, first_cycle, fac_stage);
-                    relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal,
-                                                             Two<T, R>{u1, u0, d.nC}, u0, u1, first_cycle,
-                                                             fac_stage);
+                    relax(d, gl, P.A, d.sA, 0, 0, d.nC, One<T, R>{u0}, u0, u1, first_cycle);
+                    relax(d, gl, P.A, d.sA, 0, d.nC, d.nReal, Two<T, R>{u1, u0, d.nC}, u0, u1, first_cycle);
                 }
                 {
                     // s_l <- s_l + A_l t_l (s_0 = 0)
-                    T *__restrict__ s = Ps + d.row0 * R;
-                    const One<T, R> t = stage<SB>(B, One<T, R>{Pt + d.row0 * R}, (int64_t)d.nBar, fac_stage);
-                    rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.At, d.sAt, d.row0, 0, 0, d.nBar, t,
+                    T *__restrict__ s = Ps + (d.row0 - rb) * R;
+                    const One<T, R> t = stage<SB>(B, One<T, R>{Pt + (d.row0 - rb) * R}, (int64_t)d.nBar, fac_stage);
+                    rows_dot<CI, T, R, UNR, PF, GRP, STREAM>(B, gl, P.At, d.sAt, d.row0, 0, 0, d.nBar, t,
                                                      [&](int r, const VecR<T, R> &at) {
 #pragma unroll
                         for (int j = 0; j < R; ++j) s[r * R + j] = l == 0 ? at.v[j] : s[r * R + j] + at.v[j];
@@ -371,23 +393,45 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
                 }
                 B.sync();
                 {
-                    const One<T, R> w = stage<SB>(B, One<T, R>{Ps + d.row0 * R}, (int64_t)d.nBar, fac_stage);
-                    const One<T, R> un{U0 + dn.row0 * R};
-                    T *__restrict__ s1 = Ps + dn.row0 * R;
-                    T *__restrict__ f1 = Pf + dn.row0 * R;
+                    const One<T, R> w = stage<SB>(B, One<T, R>{Ps + (d.row0 - rb) * R}, (int64_t)d.nBar, fac_stage);
+                    const One<T, R> un{U0 + (dn.row0 - rb) * R};
+                    T *__restrict__ s1 = Ps + (dn.row0 - rb) * R;
+                    T *__restrict__ f1 = Pf + (dn.row0 - rb) * R;
+                    T *__restrict__ t1 = Pt + (dn.row0 - rb) * R;
+                    T *__restrict__ v1 = U1 + (dn.row0 - rb) * R;
+                    const T *__restrict__ l1n = Pl1 + dn.row0;
+                    const bool relaxed = l + 1 < L;
+                    // the downsweep start of level l+1 < L for a real row whose
+                    // f_{l+1} is final: u_{l+1} = 0 in U1, then on a C row the
+                    // first half-sweep's correction f / l1 (u_{l+1} = 0 makes
+                    // its row product +0). Ghost rows of U0 are not touched
+                    // (this pass still reads u_{l+1} there); the upsweep
+                    // assigns them.
+                    auto start = [&](int r) {
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            if (r < dn.nC) {
+                                const T v = f1[r * R + j] * l1n[r];
+                                v1[r * R + j] = T(0) + v;
+                                t1[r * R + j] = first_cycle ? v : t1[r * R + j] + v;
+                            } else {
+                                v1[r * R + j] = T(0);
+                            }
+                        }
+                    };
                     // s_{l+1} = R_l w_l on every row of level l+1; then, on its
                     // real rows, f_{l+1} -= A_{l+1} u_{l+1} (cycles after the
                     // first; u_{l+1} is in U0 from the previous upsweep) and
                     // f_{l+1} -= s_{l+1}
                     if (!GRP || gn <= 1) {
                         for_rows(B, 0, 0, dn.nBar, [&](int r) {
-                            const VecR<T, R> sv = view_dot_r<CI, T, R, UNR, PF>(P.R, dn.sR, dn.row0, 0, r, w);
+                            const VecR<T, R> sv = view_dot_r<CI, T, R, UNR, PF, STREAM>(P.R, dn.sR, dn.row0, 0, r, w);
 #pragma unroll
                             for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
                             if (r < dn.nReal) {
                                 if (!first_cycle) {
                                     const VecR<T, R> au =
-                                        view_dot_r<CI, T, R, UNR, PF>(P.A, dn.sA, dn.row0, 0, r, un);
+                                        view_dot_r<CI, T, R, UNR, PF, STREAM>(P.A, dn.sA, dn.row0, 0, r, un);
 #pragma unroll
                                     for (int j = 0; j < R; ++j)
                                         f1[r * R + j] = (f1[r * R + j] - au.v[j]) - sv.v[j];
@@ -395,26 +439,29 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
 #pragma unroll
                                     for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
                                 }
+                                if (relaxed) start(r);
                             }
                         });
                     } else {
                         // groups: two traversals; row r has the same owning
                         // lane in both, which reads back its own s_{l+1}
-                        rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.R, dn.sR, dn.row0, 0, 0, dn.nBar, w,
+                        rows_dot<CI, T, R, UNR, PF, GRP, STREAM>(B, gn, P.R, dn.sR, dn.row0, 0, 0, dn.nBar, w,
                                                          [&](int r, const VecR<T, R> &sv) {
 #pragma unroll
                             for (int j = 0; j < R; ++j) s1[r * R + j] = sv.v[j];
                             if (first_cycle && r < dn.nReal) {
 #pragma unroll
                                 for (int j = 0; j < R; ++j) f1[r * R + j] = f1[r * R + j] - sv.v[j];
+                                if (relaxed) start(r);
                             }
                         });
                         if (!first_cycle)
-                            rows_dot<CI, T, R, UNR, PF, GRP>(B, gn, P.A, dn.sA, dn.row0, 0, 0, dn.nReal, un,
+                            rows_dot<CI, T, R, UNR, PF, GRP, STREAM>(B, gn, P.A, dn.sA, dn.row0, 0, 0, dn.nReal, un,
                                                              [&](int r, const VecR<T, R> &au) {
 #pragma unroll
                                 for (int j = 0; j < R; ++j)
                                     f1[r * R + j] = (f1[r * R + j] - au.v[j]) - s1[r * R + j];
+                                if (relaxed) start(r);
                             });
                     }
                 }
@@ -422,8 +469,8 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
             }
             {
                 const FacLevelDesc d = D[L];
-                const T *__restrict__ f = Pf + d.row0 * R;
-                T *__restrict__ u = U0 + d.row0 * R;
+                const T *__restrict__ f = Pf + (d.row0 - rb) * R;
+                T *__restrict__ u = U0 + (d.row0 - rb) * R;
                 // u_L = A_L^{-1} f_L in FP64 over the nonzeros of the inverse:
                 // the chain starts at +0 and never returns to -0, so each
                 // skipped fma(0, f_J, s) would have left s unchanged (finite f)
@@ -440,22 +487,27 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
             for (int l = L - 1; l >= 0; --l) {
                 const FacLevelDesc d = D[l];
                 const FacLevelDesc dn = D[l + 1];
-                T *__restrict__ u0 = U0 + d.row0 * R;
-                T *__restrict__ u1 = U1 + d.row0 * R;
-                const One<T, R> un = stage<SB>(B, One<T, R>{U0 + dn.row0 * R}, (int64_t)dn.nBar, fac_stage);
+                T *__restrict__ u0 = U0 + (d.row0 - rb) * R;
+                T *__restrict__ u1 = U1 + (d.row0 - rb) * R;
+                const One<T, R> un = stage<SB>(B, One<T, R>{U0 + (dn.row0 - rb) * R}, (int64_t)dn.nBar, fac_stage);
                 const int gl = GRP ? P.grp[l] : 1;
-                // u_l += P_l u_{l+1}: real rows in U1, ghost rows in U0
-                rows_dot<CI, T, R, UNR, PF, GRP>(B, gl, P.P, d.sP, d.row0, 0, 0, d.nBar, un,
+                // u_l += P_l u_{l+1}: real rows in U1, ghost rows in U0; on
+                // l >= 1 the ghost rows, zero since this cycle's downsweep and
+                // never relaxed, are written 0 + P_l u_{l+1} (u_0 keeps its
+                // ghost values from cycle to cycle)
+                rows_dot<CI, T, R, UNR, PF, GRP, STREAM>(B, gl, P.P, d.sP, d.row0, 0, 0, d.nBar, un,
                                                  [&](int r, const VecR<T, R> &pu) {
-                    T *u = r < d.nReal ? u1 : u0;
+                    if (r < d.nReal) {
 #pragma unroll
-                    for (int j = 0; j < R; ++j) u[r * R + j] = u[r * R + j] + pu.v[j];
+                        for (int j = 0; j < R; ++j) u1[r * R + j] = u1[r * R + j] + pu.v[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < R; ++j) u0[r * R + j] = (l > 0 ? T(0) : u0[r * R + j]) + pu.v[j];
+                    }
                 });
                 B.sync();
-                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, d.nC, d.nReal,
-                                                         Two<T, R>{u1, u0, d.nReal}, u1, u0, true, fac_stage);
-                relax_pass_r<CI, T, R, UNR, PF, GRP, SB>(P, B, d, gl, P.A, d.sA, 0, 0, d.nC,
-                                                         Two<T, R>{u1, u0, d.nC}, u1, u0, true, fac_stage);
+                relax(d, gl, P.A, d.sA, 0, d.nC, d.nReal, Two<T, R>{u1, u0, d.nReal}, u1, u0, true);
+                relax(d, gl, P.A, d.sA, 0, 0, d.nC, Two<T, R>{u1, u0, d.nC}, u1, u0, true);
             }
         }
 
@@ -465,9 +517,17 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
             const int64_t i = d0.row0 + P.owned[k];
             const int64_t g = P.gmap[i];
 #pragma unroll
-            for (int j = 0; j < R; ++j) P.x[g * R + j] = P.x[g * R + j] + (double)U0[i * R + j];
+            for (int j = 0; j < R; ++j) P.x[g * R + j] = P.x[g * R + j] + (double)U0[(i - rb) * R + j];
         }
     }
+}
+
+// The work vectors in the global arrays of P (u2 is P.d).
+template <class T>
+__device__ __forceinline__ WorkVecs<T> global_vecs(const FacParams &P)
+{
+    return WorkVecs<T>{static_cast<T *>(P.u), static_cast<T *>(P.d), static_cast<T *>(P.f), static_cast<T *>(P.t),
+                       static_cast<T *>(P.s), 0};
 }
 
 // One block of 512 threads per composite grid at a time; a block claims its
@@ -499,7 +559,7 @@ __global__ void __launch_bounds__(512, MINB) k_fac_all_grids_r(FacParams P)
         __syncthreads();
         const int p = claimed;
         if (p < 0) break;
-        fac_grid_r<CI, T, R, UNR, PF, GRP, SB>(P, B, p, fac_stage);
+        fac_grid_r<CI, T, R, UNR, PF, GRP, SB>(P, B, p, global_vecs<T>(P), fac_stage);
     }
 }
 
@@ -524,7 +584,7 @@ __global__ void __launch_bounds__(1024, 2) k_fac_teams(FacParams P, FacTeams TT)
     B.nt = 32 * TT.nw[k];
     B.bar = k - k0 + 1;
     for (int j = TT.grid_off[k]; j < TT.grid_off[k + 1]; ++j)
-        fac_grid_r<CI, T, R, UNR, PF, false, 0>(P, B, TT.grid[j], nullptr);
+        fac_grid_r<CI, T, R, UNR, PF, false, 0>(P, B, TT.grid[j], global_vecs<T>(P), nullptr);
 }
 
 }  // namespace dev

@@ -110,6 +110,9 @@ __global__ void k_finish_sum(const double *__restrict__ partial, int n, double *
 
 // sell_dot with the gathered vector read through L2 (ld.global.cg): the
 // single-block chain reads vectors that it wrote itself one step earlier.
+// The single block is latency bound, so up to eight entries of the row are
+// loaded (indices, then values and gathered x) before their fmas, which stay
+// in ascending entry order.
 __device__ __forceinline__ double sell_dot_cg(const int64_t *__restrict__ soff, const uint16_t *__restrict__ rlen,
                                               const int32_t *__restrict__ col, const double *__restrict__ val,
                                               int64_t slice, int lane, int64_t row, const double *x)
@@ -119,20 +122,20 @@ __device__ __forceinline__ double sell_dot_cg(const int64_t *__restrict__ soff, 
     double s = 0.0;
     const int32_t *c = col + base;
     const double *v = val + base;
-    int k = 0;
 #pragma unroll 1
-    for (; k + 4 <= len; k += 4) {
-        const int32_t c0 = __ldg(c + 32 * (k + 0)), c1 = __ldg(c + 32 * (k + 1));
-        const int32_t c2 = __ldg(c + 32 * (k + 2)), c3 = __ldg(c + 32 * (k + 3));
-        const double v0 = __ldg(v + 32 * (k + 0)), v1 = __ldg(v + 32 * (k + 1));
-        const double v2 = __ldg(v + 32 * (k + 2)), v3 = __ldg(v + 32 * (k + 3));
-        const double x0 = __ldcg(x + c0), x1 = __ldcg(x + c1), x2 = __ldcg(x + c2), x3 = __ldcg(x + c3);
-        s = fma(v0, x0, s);
-        s = fma(v1, x1, s);
-        s = fma(v2, x2, s);
-        s = fma(v3, x3, s);
+    for (int k = 0; k < len; k += 8) {
+        int32_t ci[8];
+        double a[8], xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ci[u] = k + u < len ? __ldg(c + 32 * (k + u)) : 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = k + u < len ? __ldg(v + 32 * (k + u)) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = k + u < len ? __ldcg(x + ci[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (k + u < len) s = fma(a[u], xv[u], s);
     }
-    for (; k < len; ++k) s = fma(__ldg(v + 32 * k), __ldcg(x + __ldg(c + 32 * k)), s);
     return s;
 }
 

@@ -248,10 +248,14 @@ __device__ __forceinline__ G stage(const Block &B, const G &x, int64_t nrows, un
     return x;
 }
 
+// How a half-sweep updates t with its correction v: t += v, t = v (t_l holds
+// nothing of this iteration yet), or not at all (the last cycle's upsweep,
+// whose t nothing reads).
+constexpr int kTAdd = 0, kTAssign = 1, kTNone = 2;
+
 // One Jacobi half-sweep over the rows [r0, r1) of one set (C or F points):
 // v = (f - V u) * (1/l1) with u gathered through `src`; the row's new value
-// own + v goes to dst, and t becomes v (t_assign: t_l holds nothing of this
-// iteration yet) or t + v. dst is either the row's own buffer (in place:
+// own + v goes to dst, and t is updated by t_mode. dst is either the row's own buffer (in place:
 // the pass reads u only at rows outside the set) or the other buffer of the
 // pair, which the pass reads only outside the set; either way every read of
 // the pass sees the values from before it, as Jacobi needs, without a
@@ -270,7 +274,7 @@ template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB, bool STRE
 __device__ __forceinline__ void relax_pass_r(const FacParams &P, const WorkVecs<T> &W, const Block &B,
                                              const FacLevelDesc &d, int g, const FacViewDev &V, int64_t s0,
                                              int first, int r0, int r1, const G &src, const T *own, T *dst,
-                                             bool t_assign, unsigned char *buf)
+                                             int t_mode, unsigned char *buf)
 {
     T *__restrict__ t = W.t + (d.row0 - W.rb) * R;
     const T *__restrict__ f = W.f + (d.row0 - W.rb) * R;
@@ -282,7 +286,8 @@ __device__ __forceinline__ void relax_pass_r(const FacParams &P, const WorkVecs<
         for (int j = 0; j < R; ++j) {
             const T v = (f[r * R + j] - s.v[j]) * l1[r];
             dst[r * R + j] = own[r * R + j] + v;
-            t[r * R + j] = t_assign ? v : t[r * R + j] + v;
+            if (t_mode == kTAssign) t[r * R + j] = v;
+            else if (t_mode == kTAdd) t[r * R + j] = t[r * R + j] + v;
         }
     });
     B.sync();
@@ -305,7 +310,8 @@ __device__ __forceinline__ void relax_pass_r(const FacParams &P, const WorkVecs<
 //     columns from U0) U1 -> U0.
 // t_l is never cleared: the first write of each of its phases assigns, and
 // the s_l + A_l t_l product reads t only at real rows, which every half-sweep
-// pair writes. s_l + A_l t_l overwrites s_l, which nothing reads again
+// pair writes; the last cycle's upsweep does not write t at all (nothing
+// reads it before the next launch assigns it again). s_l + A_l t_l overwrites s_l, which nothing reads again
 // before the restriction from level l - 1 writes it in the next cycle (s_0
 // is zero in Algorithm 4, so on level 0 the product alone is stored).
 template <class CI, class T, int R, int UNR, int PF, bool GRP, int SB, bool STREAM = true>
@@ -321,8 +327,8 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
     const T *__restrict__ Pl1 = static_cast<const T *>(P.l1inv);
     // one half-sweep of level d over rows [r0, r1) of view V (slices from `first`)
     auto relax = [&](const FacLevelDesc &d, int g, const FacViewDev &V, int64_t s0, int first, int r0, int r1,
-                     const auto &src, const T *own, T *dst, bool t_assign) {
-        relax_pass_r<CI, T, R, UNR, PF, GRP, SB, STREAM>(P, W, B, d, g, V, s0, first, r0, r1, src, own, dst, t_assign,
+                     const auto &src, const T *own, T *dst, int t_mode) {
+        relax_pass_r<CI, T, R, UNR, PF, GRP, SB, STREAM>(P, W, B, d, g, V, s0, first, r0, r1, src, own, dst, t_mode,
                                                          fac_stage);
     };
     {
@@ -349,6 +355,11 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
 
         for (int c = 1; c <= P.nfac; ++c) {
             const bool first_cycle = c == 1;
+            // t in the downsweep: assigned in the first cycle, else added to
+            // the previous upsweep's; in the upsweep: assigned, or not kept
+            // at all in the last cycle
+            const int tdown = first_cycle ? kTAssign : kTAdd;
+            const int tup = c == P.nfac ? kTNone : kTAssign;
             for (int l = 0; l < L; ++l) {
                 const FacLevelDesc d = D[l];
                 const FacLevelDesc dn = D[l + 1];
@@ -358,7 +369,7 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
                 if (l > 0) {
                     // u_l = 0 and its first C half-sweep were done row by row
                     // by the restriction pass from level l - 1 (below)
-                    relax(d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, One<T, R>{u1}, u1, u1, first_cycle);
+                    relax(d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, One<T, R>{u1}, u1, u1, tdown);
                 } else if (first_cycle) {
                     // u_0 = 0 (prologue): every product of the C half-sweep is
                     // +0, so its correction is f / l1 with no row product, and
@@ -376,10 +387,10 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
                         }
                     }
                     B.sync();
-                    relax(d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, One<T, R>{u1}, u0, u1, true);
+                    relax(d, gl, P.AFc, d.sAFc, d.nC, d.nC, d.nReal, One<T, R>{u1}, u0, u1, kTAssign);
                 } else {
-                    relax(d, gl, P.A, d.sA, 0, 0, d.nC, One<T, R>{u0}, u0, u1, first_cycle);
-                    relax(d, gl, P.A, d.sA, 0, d.nC, d.nReal, Two<T, R>{u1, u0, d.nC}, u0, u1, first_cycle);
+                    relax(d, gl, P.A, d.sA, 0, 0, d.nC, One<T, R>{u0}, u0, u1, tdown);
+                    relax(d, gl, P.A, d.sA, 0, d.nC, d.nReal, Two<T, R>{u1, u0, d.nC}, u0, u1, tdown);
                 }
                 {
                     // s_l <- s_l + A_l t_l (s_0 = 0)
@@ -506,8 +517,8 @@ __device__ __forceinline__ void fac_grid_r(const FacParams &P, const Block &B, i
                     }
                 });
                 B.sync();
-                relax(d, gl, P.A, d.sA, 0, d.nC, d.nReal, Two<T, R>{u1, u0, d.nReal}, u1, u0, true);
-                relax(d, gl, P.A, d.sA, 0, 0, d.nC, Two<T, R>{u1, u0, d.nC}, u1, u0, true);
+                relax(d, gl, P.A, d.sA, 0, d.nC, d.nReal, Two<T, R>{u1, u0, d.nReal}, u1, u0, tup);
+                relax(d, gl, P.A, d.sA, 0, 0, d.nC, Two<T, R>{u1, u0, d.nC}, u1, u0, tup);
             }
         }
 

@@ -1101,8 +1101,8 @@ static amgdd_status residual_norm(amgdd_handle h, const double *b, const double 
 }
 
 // Levels whose restriction has at most this many rows are restricted by one
-// block (k_chain) instead of one grid-wide launch each; a fine level of at
-// most this many rows also has its residual computed by that block.
+// cluster of blocks (k_chain) instead of one grid-wide launch each; a fine
+// level of at most this many rows also has its residual computed there.
 static constexpr int64_t kChainRows = 4096;
 
 // First level l whose restriction R_l and all coarser ones have at most
@@ -1160,6 +1160,7 @@ static amgdd_status residual_restrict(amgdd_handle h, const double *b, const dou
     C.x = x;
     C.r = h->r_all;
     C.nrm2 = h->scal;
+    C.partial = h->partial;
     chain_steps(h, h->r_all, 0, C);
     CK(launch_chain(C, st), "residual and restriction chain kernel");
     h->launches += 1;

@@ -139,11 +139,24 @@ __device__ __forceinline__ double sell_dot_cg(const int64_t *__restrict__ soff, 
     return s;
 }
 
-// The work of ChainParams on one block of 1024 threads (32 warps, one SELL
-// slice per warp at a time).
-__global__ void __launch_bounds__(1024, 1) k_chain(ChainParams C)
+// Barrier between the steps of the chain: the whole cluster (release and
+// acquire at cluster scope, so every block sees what the others wrote in
+// global memory) or, launched without a cluster, the block.
+template <bool CL>
+__device__ __forceinline__ void chain_sync()
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if constexpr (CL)
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    else __syncthreads();
+}
+
+// The work of ChainParams on one cluster of blocks (CL) or one block, one SELL
+// slice per warp at a time, the cluster's warps numbered block by block.
+template <bool CL>
+__global__ void __launch_bounds__(512, 2) k_chain(ChainParams C)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const int warp = (int)blockIdx.x * nwb + wib, nw = (int)gridDim.x * nwb;
     if (C.residual) {
         const SellView &A = C.A;
         const int64_t nslices = (A.rows + 31) / 32;
@@ -160,14 +173,20 @@ __global__ void __launch_bounds__(1024, 1) k_chain(ChainParams C)
         }
         __shared__ double red[32];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) red[warp] = acc;
+        if (lane == 0) red[wib] = acc;
         __syncthreads();
-        if (warp == 0) {
-            double v = lane < nw ? red[lane] : 0.0;
+        if (wib == 0) {
+            double v = lane < nwb ? red[lane] : 0.0;
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) C.nrm2[0] = v;
+            if (lane == 0) C.partial[blockIdx.x] = v;
         }
-        __syncthreads();
+        chain_sync<CL>();
+        // the blocks' partial sums in block order
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double t = 0.0;
+            for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(C.partial + k);
+            C.nrm2[0] = t;
+        }
     }
     for (int k = 0; k < C.nsteps; ++k) {
         const ChainStep &S = C.step[k];
@@ -179,7 +198,7 @@ __global__ void __launch_bounds__(1024, 1) k_chain(ChainParams C)
                 S.y[i] = sell_dot_cg(S.M.soff, S.M.rlen, S.M.col, S.M.val, q, lane, row, S.x);
             }
         }
-        __syncthreads();
+        if (k + 1 < C.nsteps) chain_sync<CL>();
     }
 }
 
@@ -614,7 +633,35 @@ cudaError_t launch_residual(const SellView &A, const double *b, const double *x,
 cudaError_t launch_chain(const ChainParams &C, cudaStream_t st)
 {
     if (!C.residual && C.nsteps <= 0) return cudaSuccess;
-    dev::k_chain<<<1, 1024, 0, st>>>(C);
+    // a cluster of kChainBlocks blocks when the device can hold one, else
+    // one block (cached per device)
+    static int cluster_ok[64];   // 0 unknown, 1 cluster, 2 single block
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int &ok = cluster_ok[dev & 63];
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)kChainBlocks;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)kChainBlocks, 1, 1);
+    cfg.blockDim = dim3(512, 1, 1);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (ok == 0) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, dev::k_chain<true>, &cfg);
+        if (e != cudaSuccess) return e;
+        ok = n >= 1 ? 1 : 2;
+    }
+    if (ok == 1) {
+        if ((e = cudaLaunchKernelEx(&cfg, dev::k_chain<true>, C)) != cudaSuccess) return e;
+    } else {
+        dev::k_chain<false><<<1, 512, 0, st>>>(C);
+    }
     return cudaGetLastError();
 }
 

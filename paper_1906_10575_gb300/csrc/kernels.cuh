@@ -96,11 +96,14 @@ struct FacParams {
 cudaError_t launch_residual(const SellView &A, const double *b, const double *x, double *r, double *partial,
                             int nblocks, double *out, cudaStream_t st);
 
-// One block's worth of small sparse products, run back to back by a single
-// block of 1024 threads with a block barrier between them (no launch and no
-// grid-wide wait per step): optionally r = b - A x with sum r_i^2 in *nrm2,
+// Small sparse products run back to back by one cluster of kChainBlocks
+// blocks of 512 threads (one block where the device cannot hold the
+// cluster), with a cluster barrier between them (no launch and no grid-wide
+// wait per step): optionally r = b - A x with sum r_i^2 in *nrm2 (the
+// blocks' partial sums in partial[0 .. kChainBlocks), added in block order),
 // then y = M x for each step in order (step k may read what step k - 1
 // wrote). Each row keeps the ascending fma chain of the multi-block kernels.
+constexpr int kChainBlocks = 8;
 struct ChainStep {
     SellView M;
     const double *x;
@@ -110,7 +113,7 @@ struct ChainParams {
     int residual;               // 1: the residual comes first
     SellView A;
     const double *b, *x;
-    double *r, *nrm2;
+    double *r, *nrm2, *partial;
     int nsteps;
     ChainStep step[kMaxLevels];
 };

@@ -196,6 +196,37 @@ def test_no_convergence_status_and_last_iterate():
     s.close()
 
 
+@pytest.mark.parametrize("method", ["amgdd", "vcycle"])
+def test_solve_graph_limits_and_recapture(method):
+    """A whole solve is one graph whose iterations run in a device-side while
+    node: max_iter = 0 runs no iteration (x unchanged, history[0] only, no
+    convergence unless x_0 already meets tol); a solve is re-captured when
+    tol or max_iter change, and each stops exactly where the oracle's history
+    first meets its tolerance; a larger max_iter than any before grows the
+    device history."""
+    rp, ci, v, part, nsub, pad, b = _case("poisson2d_64")
+    o = Oracle(rp, ci, v, part, nsub, pad)
+    s = Solver(rp, ci, v, part, nsub, pad)
+    solve = s.solve if method == "amgdd" else s.vcycle_solve
+    if method == "amgdd":
+        _, ho = o.amgdd_solve(b, 2, tol=1e-12, maxit=300)
+    else:
+        _, ho = o.vcycle_solve(b, tol=1e-12, maxit=300)
+    bd = _dev(b)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.AmgddError) as e:
+        solve(bd, x, tol=1e-8, max_iter=0)
+    assert e.value.status == 6 and not _host(x).any()
+    for tol, max_iter in ((1e-4, 100), (1e-8, 100), (1e-8, 300), (1e-12, 300)):
+        x.zero_()
+        info = solve(bd, x, tol=tol, max_iter=max_iter)
+        k = next(i for i, h in enumerate(ho) if h <= tol)
+        assert info["iterations"] == k, (tol, max_iter)
+        assert np.allclose(info["history"][:k + 1], ho[:k + 1], rtol=1e-12, atol=0)
+        assert info["final_relres"] == info["history"][k]
+    s.close()
+
+
 @pytest.mark.parametrize("case", ["poisson3d_24", "ragged2d", "kappa3d"])
 @pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_fac_schedules_identical(schedule, case):

@@ -237,7 +237,16 @@ amgdd_status amgdd_iterate(amgdd_handle h, const double *b, double *x, void *str
 
 /* AMG-DD solver: iterate until ||b - A x|| / ||b|| <= tol or max_iter
  * iterations. x holds x_0 on entry and the last iterate on exit (also on
- * NO_CONVERGENCE). b, x: DEVICE. info may be NULL. */
+ * NO_CONVERGENCE). b, x: DEVICE. info may be NULL.
+ * The whole solve runs as one CUDA graph on `stream`: |b|^2, the first
+ * residual and its restriction, then the iterations in a conditional while
+ * node whose condition a one-thread kernel sets from the relative residual
+ * (so no host round trip per iteration). The graph is captured on the
+ * handle's own streams the first time a (b, x, tol, max_iter) combination is
+ * used and kept until one of them changes or the FAC kernel choice changes.
+ * The call then waits for the stream and reads the iteration count and the
+ * history; it cannot itself be recorded into a caller's stream capture.
+ * max_iter >= 0 (0 computes the initial relative residual only). */
 amgdd_status amgdd_solve(amgdd_handle h, const double *b, double *x, double tol, int32_t max_iter,
                          void *stream, amgdd_solve_info *info);
 
@@ -245,7 +254,8 @@ amgdd_status amgdd_solve(amgdd_handle h, const double *b, double *x, double tol,
  * applied in place to x with right-hand side b. b, x: DEVICE. */
 amgdd_status amg_vcycle(amgdd_handle h, const double *b, double *x, void *stream);
 
-/* V-cycle solver on the same hierarchy, same stopping rule as amgdd_solve. */
+/* V-cycle solver on the same hierarchy, same stopping rule and the same
+ * one-graph execution as amgdd_solve. */
 amgdd_status amg_vcycle_solve(amgdd_handle h, const double *b, double *x, double tol,
                               int32_t max_iter, void *stream, amgdd_solve_info *info);
 

@@ -68,15 +68,15 @@ def _fac_kernel(candidate):
     return "k_fac_cluster" if candidate >= 28 else "k_fac_all_grids_r"
 
 
-def _measured_traffic(n_edge, kernel, candidate):
-    """DRAM bytes per FAC launch from the committed ncu summary of the 128^3
-    workload for this kernel, when that summary was taken with the same
-    candidate and the kernel source is unchanged since (sha1); None
-    otherwise."""
-    if n_edge != 128:
+def _measured_traffic(workload, kernel, candidate):
+    """DRAM bytes per FAC launch from the committed ncu summary of this
+    workload (profiles/<kernel>_<workload>_dram.md) for this kernel, when
+    that summary was taken with the same candidate and the kernel source is
+    unchanged since (sha1); None otherwise."""
+    if workload is None:
         return None
     import hashlib
-    summ = os.path.join(ROOT, "profiles", "%s_poisson3d_128_dram.md" % kernel)
+    summ = os.path.join(ROOT, "profiles", "%s_%s_dram.md" % (kernel, workload))
     src = os.path.join(ROOT, "paper_1906_10575_gb300", "csrc", FAC_KERNELS[kernel])
     try:
         txt = open(summ).read()
@@ -449,6 +449,20 @@ def run_extra(args, name, stream, dist, local):
         vec = sum(4.0 * 8 * (st.comp_real[l] + st.comp_ghost[l]) for l in range(L)) * w["n_fac"]
         fac_b = fac_b + (nrhs - 1) * vec
     fac_gbs = fac_b / (fac_ms * 1e-3) / 1e9
+    fac_kern = _fac_kernel(tune["best_candidate"] if tune else (None if not multi else 9))
+    fac_cand = tune["best_candidate"] if tune else None
+    fac_line = {"kernel": fac_kern, "candidate": fac_cand, "ms_per_launch": round(fac_ms, 3),
+                "algorithmic_bytes": fac_b, "achieved_gbs": round(fac_gbs, 1), "peak_gbs": hbm,
+                "hbm_frac": None if small else round(fac_gbs / hbm, 4),
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
+    # DRAM traffic of the committed ncu capture of this workload and kernel
+    # (1 pass, full size), when it matches the current source and candidate
+    traffic = _measured_traffic("batched_64" if multi and args.nsys == 64 and args.padding < 0 else None,
+                                fac_kern, fac_cand)
+    if traffic is not None:
+        fac_line["traffic"] = traffic
+        fac_line["dram_gbs"] = round(traffic / (fac_ms * 1e-3) / 1e9, 1)
+        fac_line["dram_frac"] = round(traffic / (fac_ms * 1e-3) / 1e9 / hbm, 4)
     err = None
     if not multi and prec == 1 and not args.no_fp64_check:
         # FP64 AMG-DD on the same problem: reference solution for the error
@@ -493,10 +507,7 @@ def run_extra(args, name, stream, dist, local):
         "amgdd_over_vcycle_time": round(ms / v_ms, 3),
         "ms_per_iteration": {"amgdd": round(ms / max(1, info["iterations"]), 4),
                              "vcycle": round(v_ms / max(1, sum(v_it)), 4)},
-        "fac": {"kernel": _fac_kernel(tune["best_candidate"] if tune else (None if not multi else 9)),
-                "candidate": tune["best_candidate"] if tune else None, "ms_per_launch": round(fac_ms, 3),
-                "algorithmic_bytes": fac_b, "achieved_gbs": round(fac_gbs, 1), "peak_gbs": hbm,
-                "hbm_frac": None if small else round(fac_gbs / hbm, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+        "fac": fac_line,
         "composite_overhead": round(st.composite_overhead, 3), "levels": st.num_levels,
         "coarsest": int(st.n[st.num_levels - 1]), "setup_s": round(setup_s, 1),
         "device_gb": round(st.device_bytes / 1e9, 2),
@@ -885,7 +896,8 @@ def main():
     # the fmas the kernel executes (zero entries skipped), is reported beside
     kern = _fac_kernel(cand)
     roof = {"bound": "hbm", "achieved": round(fac_gbs, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(frac_hbm, 4), "traffic": _measured_traffic(args.n, kern, cand),
+            "frac": round(frac_hbm, 4), "traffic": _measured_traffic("poisson3d_128" if args.n == 128 and args.padding < 0 and
+                                         args.coarsen == "rs" and args.interp == "direct" else None, kern, cand),
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
             "kernel": kern, "candidate": cand, "ms_per_launch": round(fac_ms, 3),
             "algorithmic_bytes": fac_b,

@@ -1146,14 +1146,24 @@ static amgdd_status restrict_all(amgdd_handle h, double *r_all, cudaStream_t st)
 // The right-hand sides of an AMG-DD iteration: r = b - A x (its squared
 // norm in h->scal[0]) and r_l = R_{l-1} r_{l-1} on every level, into r_all.
 // A fine level of at most kChainRows rows does all of it in one block.
-static amgdd_status residual_restrict(amgdd_handle h, const double *b, const double *x, cudaStream_t st)
+// chk (may be null): the convergence check of a solve graph, done by the
+// single chain launch when the fine level is small enough for it; *checked
+// says whether it was (else the caller launches the check itself).
+static amgdd_status residual_restrict(amgdd_handle h, const double *b, const double *x, cudaStream_t st,
+                                      const ChainCheck *chk = nullptr, bool *checked = nullptr)
 {
+    if (checked) *checked = false;
     if (h->lev[0].n > kChainRows) {
         CK(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, st), "residual kernel");
         h->launches += 2;
         return restrict_all(h, h->r_all, st);
     }
     ChainParams C{};
+    if (chk) {
+        C.check = *chk;
+        C.check.on = 1;
+        if (checked) *checked = true;
+    }
     C.residual = 1;
     C.A = h->lev[0].A;
     C.b = b;
@@ -1414,21 +1424,33 @@ static amgdd_status capture_solve(amgdd_handle h, int method, const double *b, d
         return s == AMGDD_OK;
     };
     cudaStreamCaptureStatus cst;
+    // the check of the first residual (first = 1) and of every iteration's
+    ChainCheck chk{};
+    chk.first = 1;
+    chk.max_iter = max_iter;
+    chk.tol = tol;
+    chk.ref2 = h->scal + 1;
+    chk.cs = h->conv;
+    chk.hist = h->hist;
+    bool folded = false;
     if (step(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph), "capture info") &&
-        step(cudaGraphConditionalHandleCreate(&hc, graph, 0, 0), "conditional handle") &&
-        step(launch_sumsq(b, h->lev[0].n, h->partial, h->nred, h->scal + 1, cs), "norm kernel")) {
-        h->launches += 2;
-        if (amgdd) {
-            s = residual_restrict(h, b, x, cs);
-        } else {
-            step(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs), "residual kernel");
+        step(cudaGraphConditionalHandleCreate(&hc, graph, 0, 0), "conditional handle")) {
+        chk.hc = hc;
+        if (step(launch_sumsq(b, h->lev[0].n, h->partial, h->nred, h->scal + 1, cs), "norm kernel")) {
             h->launches += 2;
+            if (amgdd) {
+                s = residual_restrict(h, b, x, cs, &chk, &folded);
+            } else {
+                step(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs),
+                     "residual kernel");
+                h->launches += 2;
+            }
         }
     }
-    if (step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 1, cs), "check kernel")) {
+    if (!folded && step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 1, cs),
+                        "check kernel"))
         h->launches += 1;
-        G.pre_launches = h->launches - l0;
-    }
+    G.pre_launches = h->launches - l0;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     cudaGraphNode_t wnode = nullptr;
@@ -1446,12 +1468,15 @@ static amgdd_status capture_solve(amgdd_handle h, int method, const double *b, d
              "begin body capture")) {
         const int64_t l1 = h->launches;
         s = amgdd ? fac(h, h->r_all, x, cs2) : method == 1 ? vcycle(h, b, x, cs2) : vcycle_hybrid(h, b, x, cs2);
-        if (s == AMGDD_OK && amgdd) s = residual_restrict(h, b, x, cs2);
+        chk.first = 0;
+        bool folded_body = false;
+        if (s == AMGDD_OK && amgdd) s = residual_restrict(h, b, x, cs2, &chk, &folded_body);
         if (s == AMGDD_OK && !amgdd) {
             step(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs2), "residual kernel");
             h->launches += 2;
         }
-        if (step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 0, cs2), "check kernel"))
+        if (!folded_body &&
+            step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 0, cs2), "check kernel"))
             h->launches += 1;
         G.body_launches = h->launches - l1;
         cudaGraph_t body = nullptr;

@@ -139,6 +139,26 @@ __device__ __forceinline__ double sell_dot_cg(const int64_t *__restrict__ soff, 
     return s;
 }
 
+// One convergence check of a solve graph's while node (one thread): rel =
+// sqrt(nr2) / ref (first: k = 0, ref = sqrt(*ref2), or the residual norm
+// itself when that is zero), hist[k] = rel, the node's condition set to
+// "rel > tol (or NaN) and k < max_iter", k advancing by the iteration
+// about to run.
+__device__ __forceinline__ void converge_step(cudaGraphConditionalHandle hc, double nr2, const double *ref2,
+                                              ConvState *cs, double *hist, double tol, int32_t max_iter, int first)
+{
+    const double nr = sqrt(nr2);
+    int32_t k = first ? 0 : cs->k;
+    double ref = first ? sqrt(ref2[0]) : cs->ref;
+    if (first && ref == 0.0) ref = nr;
+    const double rel = ref > 0.0 ? nr / ref : 0.0;
+    hist[k] = rel;
+    const bool more = !(rel <= tol) && k < max_iter;
+    cs->k = more ? k + 1 : k;
+    cs->ref = ref;
+    cudaGraphSetConditional(hc, more ? 1u : 0u);
+}
+
 // Barrier between the steps of the chain: the whole cluster (release and
 // acquire at cluster scope, so every block sees what the others wrote in
 // global memory) or, launched without a cluster, the block.
@@ -186,6 +206,8 @@ __global__ void __launch_bounds__(512, 2) k_chain(ChainParams C)
             double t = 0.0;
             for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(C.partial + k);
             C.nrm2[0] = t;
+            const ChainCheck &K = C.check;
+            if (K.on) converge_step(K.hc, t, K.ref2, K.cs, K.hist, K.tol, K.max_iter, K.first);
         }
     }
     for (int k = 0; k < C.nsteps; ++k) {
@@ -206,16 +228,7 @@ __global__ void k_converge(cudaGraphConditionalHandle hc, const double *nrm2, co
                            double *hist, double tol, int32_t max_iter, int first)
 {
     if (threadIdx.x != 0) return;
-    const double nr = sqrt(nrm2[0]);
-    int32_t k = first ? 0 : cs->k;
-    double ref = first ? sqrt(ref2[0]) : cs->ref;
-    if (first && ref == 0.0) ref = nr;
-    const double rel = ref > 0.0 ? nr / ref : 0.0;
-    hist[k] = rel;
-    const bool more = !(rel <= tol) && k < max_iter;
-    cs->k = more ? k + 1 : k;
-    cs->ref = ref;
-    cudaGraphSetConditional(hc, more ? 1u : 0u);
+    converge_step(hc, nrm2[0], ref2, cs, hist, tol, max_iter, first);
 }
 
 // y[i] = M_i . x (mode 0) or y[i] = y[i] + M_i . x (mode 1) over rows [r0, r1).

@@ -109,6 +109,18 @@ struct ChainStep {
     const double *x;
     double *y;
 };
+struct ConvState;
+// The convergence check of a solve graph's while node (see launch_converge),
+// done by the chain itself right after the norm when `on` is set.
+struct ChainCheck {
+    int on, first;
+    int32_t max_iter;
+    double tol;
+    cudaGraphConditionalHandle hc;
+    const double *ref2;
+    ConvState *cs;
+    double *hist;
+};
 struct ChainParams {
     int residual;               // 1: the residual comes first
     SellView A;
@@ -116,6 +128,7 @@ struct ChainParams {
     double *r, *nrm2, *partial;
     int nsteps;
     ChainStep step[kMaxLevels];
+    ChainCheck check;           // only with the residual
 };
 cudaError_t launch_chain(const ChainParams &C, cudaStream_t st);
 

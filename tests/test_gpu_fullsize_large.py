@@ -68,6 +68,12 @@ def test_kappa256_mixed_sampled():
         own, ref = _owned_update(o, w, rl, p)
         assert np.array_equal(xg[own], ref), (best, p)
     assert np.count_nonzero(xg) > 0.99 * s.n
+    # the teams kernel with lists of grids (4096 grids for 304 blocks of
+    # 1024 threads: two teams of 16 warps each) gives the same x everywhere
+    capi.amgdd_set_fac_kernel(s.h, 1, 31)
+    x31 = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    capi.amgdd_iterate(s.h, bd, x31)
+    assert np.array_equal(x31.cpu().numpy(), xg)
     s.close()
 
 

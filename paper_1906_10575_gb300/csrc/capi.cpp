@@ -1447,8 +1447,8 @@ static amgdd_status capture_solve(amgdd_handle h, int method, const double *b, d
             }
         }
     }
-    if (!folded && step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 1, cs),
-                        "check kernel"))
+    if (s == AMGDD_OK && !folded &&
+        step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 1, cs), "check kernel"))
         h->launches += 1;
     G.pre_launches = h->launches - l0;
     const cudaGraphNode_t *deps = nullptr;
@@ -1475,7 +1475,7 @@ static amgdd_status capture_solve(amgdd_handle h, int method, const double *b, d
             step(launch_residual(h->lev[0].A, b, x, h->r_all, h->partial, h->nred, h->scal, cs2), "residual kernel");
             h->launches += 2;
         }
-        if (!folded_body &&
+        if (s == AMGDD_OK && !folded_body &&
             step(launch_converge(hc, h->scal, h->scal + 1, h->conv, h->hist, tol, max_iter, 0, cs2), "check kernel"))
             h->launches += 1;
         G.body_launches = h->launches - l1;

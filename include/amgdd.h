@@ -209,6 +209,21 @@ amgdd_status amgdd_get_cf(amgdd_handle h, int32_t level, int32_t *cf, double *l1
 /* Row-major explicit inverse of the coarsest matrix (HOST, n_L*n_L). */
 amgdd_status amgdd_get_coarse_inverse(amgdd_handle h, double *ainv);
 
+/* The team plan of FAC candidate 31 (no counterpart in the paper; the host
+ * planner setup uses, exposed for inspection, no handle, no GPU): nsub
+ * composite grids with work[g] (FMA counts, HOST) over nblocks blocks of 32
+ * warps, at most 15 teams per block. Up to two grids per block on average,
+ * every grid gets a team of its own whose warps follow its work; with more
+ * grids, every block has two teams of 16 warps with lists of grids (largest
+ * first, each to the least-loaded team). Outputs (HOST, caller-allocated):
+ * block_off[nblocks + 1] (teams of block b: [block_off[b], block_off[b+1])),
+ * w0 and nw (first warp and warps of each team; room for 15 * nblocks),
+ * grid_off (room for 15 * nblocks + 1) and grid[nsub] (the grids of team k:
+ * grid[grid_off[k] .. grid_off[k+1])), *nteams. INVALID_ARG for nsub < 1,
+ * nblocks < 1, null pointers or negative work. */
+amgdd_status amgdd_plan_teams(const int64_t *work, int32_t nsub, int32_t nblocks, int32_t *block_off,
+                              int32_t *w0, int32_t *nw, int32_t *grid_off, int32_t *grid, int32_t *nteams);
+
 /* ---- solve phase (device pointers, stream-ordered) ---------------------- */
 
 /* Algorithm 2, step 1: r = b - A_0 x on all n rows; *nrm2 (HOST, may be NULL)

@@ -64,7 +64,7 @@ EXPORTS = [
     "amgdd_get_fac_state", "amgdd_iterate", "amgdd_solve", "amg_vcycle", "amg_vcycle_solve",
     "amgdd_residual_csr_noalloc", "amgdd_iterate_multi", "amgdd_fac_multi", "amgdd_solve_multi",
     "amg_hybrid_cycle", "amg_hybrid_solve", "amgdd_kappa_grad_3d",
-    "amgdd_set_fac_kernel", "amgdd_autotune",
+    "amgdd_set_fac_kernel", "amgdd_autotune", "amgdd_plan_teams",
 ]
 
 FAC_CANDIDATES = 32
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "amgdd_kappa_grad_3d": [i32, i32, i32, vp, vp, vp, vp, vp],
         "amg_hybrid_solve": [vp, vp, vp, f64, i32, vp, C.POINTER(amgdd_solve_info)],
         "amgdd_solve_multi": [vp, vp, vp, i32, f64, i32, vp, C.POINTER(amgdd_solve_info)],
+        "amgdd_plan_teams": [vp, i32, i32, vp, vp, vp, vp, vp, C.POINTER(i32)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -228,6 +229,27 @@ def amgdd_get_cf(h, level, n, with_cf=True):
     l1 = np.zeros(n, np.float64)
     _check(load().amgdd_get_cf(h, level, None if cf is None else cf.ctypes.data, l1.ctypes.data), h)
     return cf, l1
+
+
+def amgdd_plan_teams(work, nblocks):
+    """The team plan of FAC candidate 31 for per-grid work (host only): a list
+    per block of its teams as (first warp, warps, grids)."""
+    work = np.ascontiguousarray(work, np.int64)
+    nsub = len(work)
+    cap = 15 * int(nblocks)
+    block_off = np.zeros(nblocks + 1, np.int32)
+    w0 = np.zeros(cap, np.int32)
+    nw = np.zeros(cap, np.int32)
+    grid_off = np.zeros(cap + 1, np.int32)
+    grid = np.zeros(max(nsub, 1), np.int32)
+    nteams = C.c_int32()
+    _check(load().amgdd_plan_teams(work.ctypes.data, nsub, int(nblocks), block_off.ctypes.data, w0.ctypes.data,
+                                   nw.ctypes.data, grid_off.ctypes.data, grid.ctypes.data, C.byref(nteams)))
+    plan = []
+    for b in range(nblocks):
+        plan.append([(int(w0[k]), int(nw[k]), [int(g) for g in grid[grid_off[k]:grid_off[k + 1]]])
+                     for k in range(block_off[b], block_off[b + 1])])
+    return plan
 
 
 def amgdd_get_coarse_inverse(h, nL):

@@ -1077,6 +1077,24 @@ amgdd_status amgdd_get_cf(amgdd_handle h, int32_t level, int32_t *cf, double *l1
     return AMGDD_OK;
 }
 
+amgdd_status amgdd_plan_teams(const int64_t *work, int32_t nsub, int32_t nblocks, int32_t *block_off,
+                              int32_t *w0, int32_t *nw, int32_t *grid_off, int32_t *grid, int32_t *nteams)
+{
+    if (!work || nsub < 1 || nblocks < 1 || !block_off || !w0 || !nw || !grid_off || !grid || !nteams)
+        return fail(nullptr, AMGDD_ERR_INVALID_ARG, "bad team plan arguments");
+    std::vector<int64_t> wv(work, work + nsub);
+    for (int64_t x : wv)
+        if (x < 0) return fail(nullptr, AMGDD_ERR_INVALID_ARG, "negative work");
+    const TeamPlan T = plan_teams(wv, nblocks);
+    std::copy(T.block_off.begin(), T.block_off.end(), block_off);
+    std::copy(T.w0.begin(), T.w0.end(), w0);
+    std::copy(T.nw.begin(), T.nw.end(), nw);
+    std::copy(T.grid_off.begin(), T.grid_off.end(), grid_off);
+    std::copy(T.grid.begin(), T.grid.end(), grid);
+    *nteams = (int32_t)T.w0.size();
+    return AMGDD_OK;
+}
+
 amgdd_status amgdd_get_coarse_inverse(amgdd_handle h, double *ainv)
 {
     if (!h || !ainv) return fail(h, AMGDD_ERR_INVALID_ARG, "null argument");

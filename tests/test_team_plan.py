@@ -38,7 +38,7 @@ def _box_work(nb):
 
 
 def test_one_grid_per_team_balances_work():
-    w = _box_work(8)                       # 512 grids, the 128^3 headline's boxes
+    w = _box_work(8)                       # 512 grids: 16^3 boxes of a 128^3 grid
     nblocks = 304                          # two blocks of 1024 threads per SM
     plan = capi.amgdd_plan_teams(w, nblocks)
     _check_invariants(plan, len(w))

@@ -330,7 +330,7 @@ def _ev_ms(stream, fn, k=1):
     return a0.elapsed_time(a1) / k
 
 
-def run_extra(args, name, stream, dist, local):
+def run_extra(args, name, stream, dist, local, emit=True):
     """The other configurations, one JSON line each (not the headline):
 
     kappa3d_256 -- 256^3 variable-coefficient diffusion, 4096 composite grids,
@@ -517,7 +517,9 @@ def run_extra(args, name, stream, dist, local):
     }
     if multi:
         line["edges"] = list(map(int, w["edges"]))
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
 def run_adjoint(args, stream):
@@ -607,6 +609,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the four-right-hand-side measurement")
+    ap.add_argument("--no-small-case", action="store_true",
+                    help="skip the 2D 64^2 measurement reported beside the headline")
     ap.add_argument("--hybrid-level", type=int, default=6,
                     help="switch level of the hybrid AMG-DD measurement (0 = skip)")
     ap.add_argument("--schedule", type=int, default=0, help="FAC kernel variant (0 = library default)")
@@ -941,6 +945,22 @@ def main():
         "multi_rhs": multi,
         "hybrid": hybrid,
     }
+    if not args.no_small_case:
+        # the small latency-bound case (2D 64^2, where AMG-DD beats the
+        # V-cycle on one GPU), measured in the same run beside the headline
+        sa = argparse.Namespace(**vars(args))
+        sa.padding, sa.candidate, sa.interp, sa.coarsen, sa.edge = -1, -1, "direct", "rs", 0
+        sa.steps, sa.warmup, sa.no_autotune, sa.schedule = 5, 3, False, 0
+        sl = run_extra(sa, "poisson2d_64", stream, dist, local, emit=False)
+        line["small_case"] = {
+            "workload": sl["config"]["workload"], "l2_policy": sl["config"]["l2_policy"],
+            "amgdd_ms": sl["value"], "amgdd_iterations": sl["iterations"],
+            "vcycle_ms": sl["vcycle_fp64"]["ms_all_columns"],
+            "vcycle_iterations": sl["vcycle_fp64"]["iterations"][0],
+            "amgdd_over_vcycle_time": sl["amgdd_over_vcycle_time"], "ms_per_iteration": sl["ms_per_iteration"],
+            "fac_kernel": sl["fac"]["kernel"], "fac_candidate": sl["fac"]["candidate"],
+            "fac_ms_per_launch": sl["fac"]["ms_per_launch"],
+            "launches_per_solve": sl["gpu_launches_per_step"]}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, it_dd, args.interp, args.coarsen)
     if rank == 0:

@@ -76,8 +76,10 @@ typedef struct {
                                checked and dropped chunk by chunk, the way a
                                device setup streams it to the device */
     int32_t threads;        /* FAC kernel threads per block (0 = default 512) */
-    int32_t schedule;       /* FAC kernel variant, all giving identical results:
-                               0 = default (8); 1 = four resident blocks of 512
+    int32_t schedule;       /* single-column FAC kernel schedule, all giving
+                               identical results: 0 = none (the default
+                               kernel is candidate 15 of amgdd_autotune at
+                               every width); 1 = four resident blocks of 512
                                threads per SM; 2 = three blocks, deeper
                                unrolling; 3-5 = operators staged through
                                cp.async rings of different depths; 6, 7 = two
@@ -363,7 +365,9 @@ amgdd_status amgdd_solve_multi(amgdd_handle h, const double *B, double *X, int32
  *               grid per team while there are at most two grids per block,
  *               else two teams of 16 warps per block with lists of grids;
  *               16-bit local columns).
- * Defaults: k = 7 (schedule 8) for one column, k = 9 for 2 and 4. */
+ * Default before any amgdd_set_fac_kernel or amgdd_autotune: k = 15 for
+ * every width (k = schedule - 1 for one column when amgdd_options.schedule
+ * is 1..9). */
 #define AMGDD_FAC_CANDIDATES 32
 /* amgdd_autotune flags: also time candidates 18 and 19 (reordered row sums) */
 #define AMGDD_TUNE_ALLOW_REORDERED 1

@@ -99,7 +99,7 @@ struct amgdd_handle_s {
     // FAC kernel candidate per column count (index 0: 1 column, 1: 2, 2: 4),
     // numbered as in amgdd_autotune; and the lanes per row of each level that
     // the group-per-row candidate uses (chosen from the level sizes at setup)
-    int fac_cand[3] = {7, 9, 9};
+    int fac_cand[3] = {15, 15, 15};
     int8_t grp_level[kMaxLevels + 1] = {};
     const int32_t *one_bin_off = nullptr;   // {0, nsub}: every grid in one bin (global queue)
     int hyb_level = -1;
@@ -537,7 +537,9 @@ static cudaError_t upload_fac(amgdd_handle h, FacLayout &F, FacStream &S, int nl
     // (up to 32) while the level's mean slices per grid times g stay below
     // the 16 warps of a block and 2g entries still fit the mean real row
     if (&P == &h->fac) {
-        h->fac_cand[0] = P.schedule - 1;   // the options' schedule until changed
+        // a single-column schedule asked for in the options, else candidate 15
+        // (two operator entries in flight, four blocks per SM, L2 prefetch)
+        h->fac_cand[0] = h->opt.schedule >= 1 && h->opt.schedule <= 9 ? P.schedule - 1 : 15;
         {
             std::vector<int32_t> ob{0, nsub};
             int32_t *dob;

@@ -9,7 +9,7 @@ and corner boxes) against the oracle's AlgFAC for exactly those subdomains.
 The iteration runs with the FAC kernel the benchmark times (the autotuner's
 choice; candidates 15 and 31, the one-block-per-grid kernel and the
 work-sized warp teams, are its choices on this workload) as well as with the
-default kernel.
+single-column kernel (schedule 8).
 """
 import numpy as np
 import pytest
@@ -47,7 +47,7 @@ def test_fullsize_one_iteration_sampled(full):
     b = w["b"]
     bd = torch.from_numpy(b).cuda()
     tuned, _ = capi.amgdd_autotune(s.h, 1, reps=2)
-    kernels = sorted({7, 15, 31, tuned})    # 7: the default before tuning
+    kernels = sorted({7, 15, 31, tuned})    # 7: the single-column kernel (schedule 8)
     xs = {}
     for k in kernels:
         capi.amgdd_set_fac_kernel(s.h, 1, k)
